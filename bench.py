@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Benchmark: ALTO encode + CP-ALS (10 iterations) on the 10M x 2M x 50k,
+100M-nonzero Zipf(1.1) tensor at rank 32, on one GB300 per process.
+
+One step = one pass of the whole hot path over the tensor: encode (bit plan,
+linearization, radix sort, partition, hot rows) followed by CP-ALS with 10
+iterations (per mode: MTTKRP, Gram, fp64 solve, normalisation; fit per
+iteration), starting from the same seeded factors every step.
+
+value = MTTKRP work of the step (iterations x modes x nnz x R) / step time,
+summed over ranks (replicas: every rank runs its own copy of the workload).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MTTKRP nnz*R/s & HBM GB/s vs peak; served CP-ALS p50/p99 vs one-at-a-time"
+UNIT = "nnz*R/s"
+CONFIG_INDEX = 1
+ITERS = 10
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--nnz", type=int, default=0, help="override nonzeros (testing only)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload(args):
+    import synth
+    spec = synth.CONFIGS[CONFIG_INDEX]
+    if args.nnz:
+        spec = synth.scaled(spec, args.nnz)
+    return spec
+
+
+def config_json(spec, extra=None):
+    c = {"workload": f"encode + CP-ALS {ITERS} iters: {spec.name}",
+         "dims": list(spec.dims), "nnz": spec.nnz, "rank": spec.rank,
+         "coords": "Zipf s=1.1 per mode (rank->index permuted)", "values": "lognormal(0,1) fp32",
+         "cp_als_iters": ITERS,
+         "l2": "inputs larger than L2 (1.6 GB nonzero stream per step)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def traffic_from_profiles(kernel_src_sha):
+    """dram bytes per launch of the MTTKRP kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "mttkrp_zipf3d_10Mx2Mx50k_r32.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_src_sha:
+        return None
+    return float(t.group(1))
+
+
+def kernel_src_sha():
+    h = hashlib.sha256()
+    for f in ("mttkrp.cu", "mttkrp.cuh", "alto_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2403_06348_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes_per_mode(coords, dims, R, key_bytes, fbytes=4):
+    """M*(key+value bytes) + sum_{m!=n} D_m*R*fbytes + I_n*R*4, D_m = distinct rows."""
+    M = coords.shape[1]
+    D = [int(np.count_nonzero(np.bincount(coords[m], minlength=dims[m]))) for m in range(len(dims))]
+    out = []
+    for n in range(len(dims)):
+        b = M * (key_bytes + 4) + sum(D[m] * R * fbytes for m in range(len(dims)) if m != n)
+        b += dims[n] * R * 4
+        out.append(b)
+    return out, D
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(coords, vals, dims, R, sample_nnz, threads, modes):
+    """The oracle as it stands on the first sample_nnz nonzeros: encode, then
+    the Alg. 1 mode updates listed in ``modes`` (C fp64 MTTKRP on ``threads``
+    threads). Returns (MTTKRP work nnz*R per second of the whole sample,
+    seconds, per-part seconds)."""
+    from oracle import alto_ref as ar
+    from oracle import cref
+    import synth
+    c = np.ascontiguousarray(coords[:, :sample_nnz])
+    v = np.ascontiguousarray(vals[:sample_nnz])
+    A = [a.astype(np.float64) for a in synth.factors(dims, R, seed=7)]
+    mk = lambda cc, vv, F, n: cref.mttkrp(cc, vv, dims, F, n, nthreads=threads)
+    t0 = time.perf_counter()
+    ar.encode(c, v, dims)
+    parts = {"encode_s": time.perf_counter() - t0}
+    for n in modes:
+        t = time.perf_counter()
+        ar.cp_als_mode_update(c, v, A, n, mk)
+        parts[f"mode{n}_s"] = time.perf_counter() - t
+    secs = time.perf_counter() - t0
+    return len(modes) * sample_nnz * R / secs, secs, parts
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    spec = workload(args)
+    coords, vals = synth.cached(spec)
+    coords = np.asarray(coords)
+    vals = np.asarray(vals)
+    threads = os.cpu_count() or 1
+    sample = min(spec.nnz, 1_000_000)
+    N = len(spec.dims)
+    work = 0.0
+    t_all = 0.0
+    for i in range(args.warmup + args.steps):
+        rate, secs, _ = oracle_sample(coords, vals, spec.dims, spec.rank, sample, threads, [i % N])
+        if i >= args.warmup:
+            work += rate * secs
+            t_all += secs
+    value = work / t_all
+    sample_desc = (f"each step: oracle encode + one Alg. 1 mode update (modes in turn; C fp64 "
+                   f"MTTKRP on {threads} threads) on the first {sample} of {spec.nnz} "
+                   f"nonzeros, dims unchanged; value = MTTKRP nnz*R / time over the timed steps")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "higher_is_better": True, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / max(args.steps, 1),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_json(spec),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample_desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import paper_2403_06348_gb300 as alto
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    alto.build()
+    spec = workload(args)
+    coords, vals = synth.cached(spec)
+    coords = np.asarray(coords)
+    vals = np.asarray(vals)
+    dims, R, M, N = spec.dims, spec.rank, spec.nnz, len(spec.dims)
+
+    coords_d = torch.from_numpy(coords.view(np.int32)).cuda()
+    vals_d = torch.from_numpy(vals).cuda()
+    A0 = synth.factors(dims, R, seed=1)
+    A0d = [torch.from_numpy(a).cuda() for a in A0]
+    work = [torch.empty_like(a) for a in A0d]
+
+    def step(profile_into=None):
+        h = alto.alto_encode(coords_d, vals_d, dims)
+        if profile_into is not None:
+            h.profile_enable(True)
+        for w, a in zip(work, A0d):
+            w.copy_(a)
+        lam, fits = h.cpals(R, ITERS, work)
+        if profile_into is not None:
+            for k, (n, ms) in h.profile_read().items():
+                a, b = profile_into.get(k, (0, 0.0))
+                profile_into[k] = (a + n, b + ms)
+        info_kw = None
+        if profile_into is not None and "_kw" not in profile_into:
+            info = h.query()
+            profile_into["_kw"] = int(info.key_words)
+            profile_into["_plans"] = [h.get_mode_plan(n, R) for n in range(N)]
+        h.free()
+        return fits
+
+    for _ in range(args.warmup):
+        fits = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    prof = {}
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = alto.alto_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        fits = step(prof)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = alto.alto_kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    work_units = ITERS * N * M * R
+    value = world * work_units / (ms / 1000.0)
+
+    # roofline of the dominant kernel (the MTTKRP segment kernel)
+    kw = prof.get("_kw", 1)
+    bytes_per_mode, distinct = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw)
+    n_mttkrp, ms_mttkrp = prof.get("mttkrp", (0, 0.0))
+    avg_ms = ms_mttkrp / max(n_mttkrp, 1)
+    avg_bytes = sum(bytes_per_mode) / N
+    achieved = avg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
+    peak, peak_src = measured_peaks()
+    sha = kernel_src_sha()
+    traffic = traffic_from_profiles(sha)
+    breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps}
+                 for k, v in prof.items() if not k.startswith("_")}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": config_json(spec, {"parallelism": f"replicas x{world}",
+                                         "mode_plans": prof.get("_plans")}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "kernel": "mttkrp_kernel",
+                         "peak_source": f"{peak_src} hbm_gbs",
+                         "algorithmic_bytes_per_launch": avg_bytes,
+                         "avg_launch_ms": avg_ms, "launches": n_mttkrp,
+                         "source_sha": sha},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "breakdown_ms_per_step": breakdown,
+            "final_fit": fits[-1] if fits else None}
+
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(args, alto, coords, vals, spec, A0, world, barrier)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        sample = min(M, 2_000_000)
+        rate, secs, parts = oracle_sample(coords, vals, dims, R, sample, threads, list(range(N)))
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": (f"oracle encode + one CP-ALS iteration (all {N} mode "
+                                           f"updates, C fp64 MTTKRP) on the first {sample} of {M} "
+                                           f"nonzeros, dims unchanged: {secs:.1f} s; "
+                                           + ", ".join(f"{k} {v:.2f}" for k, v in parts.items()))}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, alto, coords, vals, spec, A0, world, barrier):
+    """Same step through the C ABI with pinned HOST buffers: the library copies
+    coords/values/factors in and the factors, lambda and fits out."""
+    import torch
+    dims, R, M, N = spec.dims, spec.rank, spec.nnz, len(spec.dims)
+    ch = torch.from_numpy(coords.view(np.int32)).pin_memory()
+    vh = torch.from_numpy(vals).pin_memory()
+    Ah = [torch.from_numpy(a).pin_memory() for a in A0]
+    work = [torch.empty_like(a).pin_memory() for a in Ah]
+    cn, vn = ch.numpy(), vh.numpy()
+    wn = [w.numpy() for w in work]
+
+    def step():
+        h = alto.alto_encode(cn, vn, dims)
+        for w, a in zip(work, Ah):
+            w.copy_(a)
+        h.cpals(R, ITERS, wn)
+        h.free()
+
+    step()
+    steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / steps
+    ms = ev0.elapsed_time(ev1) / steps
+    ms = max(ms, wall * 1000.0)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    h2d = coords.nbytes + vals.nbytes + sum(a.nbytes for a in A0)
+    d2h = sum(a.nbytes for a in A0) + 8 * R + 8 * ITERS
+    return {"value": world * ITERS * N * M * R / (ms / 1000.0), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms,
+            "steps": steps}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,264 @@
+/*
+ * alto.h -- C ABI of the GB300 (sm_103a) ALTO sparse-tensor library.
+ *
+ * The library encodes a sparse tensor given in coordinate form into the ALTO
+ * format (Adaptive Linearized Tensor Order, arXiv 2403.06348, Section III-A),
+ * computes the mode-agnostic MTTKRP over that single encoded copy (Alg. 1
+ * MTTKRP line, Alg. 3 and Alg. 4) and runs CP-ALS on top of it (Alg. 1).
+ * Every step runs in the library's own CUDA kernels; there is no CPU
+ * fallback.
+ *
+ * Conventions shared by every call:
+ *  - Coordinates are 0-based. Mode n has length dims[n] (1 <= dims[n] < 2^32).
+ *  - Dense matrices are row-major: A^(n) is dims[n] x R, element (i, r) at
+ *    A[i * R + r]. They must be 16-byte aligned.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls enqueue work on that stream and return without waiting,
+ *    unless the call says it synchronises.
+ *  - A handle is used by one stream at a time; calls on one handle from two
+ *    streams at once race.
+ *  - Return values are alto_status codes. On failure alto_last_error() gives
+ *    a message for the calling thread. Argument errors are detected before
+ *    any work is enqueued and leave outputs untouched.
+ *  - nnz < 2^32 in this version.
+ */
+#ifndef ALTO_H_
+#define ALTO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ALTO_MAX_MODES 8
+#define ALTO_MAX_RANK 64
+#define ALTO_MAX_HOT 4096
+
+typedef enum alto_status {
+  ALTO_OK = 0,
+  ALTO_ERR_INVALID_ARG = -1,   /* bad pointer, size, mode, rank or alignment   */
+  ALTO_ERR_OOM = -2,           /* the allocator returned NULL                   */
+  ALTO_ERR_CUDA = -3,          /* a CUDA runtime call failed                    */
+  ALTO_ERR_UNSUPPORTED = -4,   /* > 128 index bits, rank not in {4,8,16,32,64}  */
+  ALTO_ERR_COORD_RANGE = -5,   /* a coordinate >= dims[n] (detected on device)  */
+  ALTO_ERR_NOT_SPD = -6,       /* CP-ALS: V of Alg. 1 not positive definite     */
+  ALTO_ERR_TIMEOUT = -7        /* a bounded device wait gave up                 */
+} alto_status;
+
+/* Element type of factor matrices handed to alto_mttkrp. */
+typedef enum alto_dtype { ALTO_F32 = 0, ALTO_BF16 = 1 } alto_dtype;
+
+/* Output strategy of one mode's MTTKRP (Section IV-B, Alg. 4).
+ *  ATOMIC: nonzeros are streamed in ALTO order; runs of equal output row are
+ *          summed in registers; the most reused rows of the mode ("hot rows",
+ *          picked at encode time) are staged in shared memory per line
+ *          segment and flushed once per segment; all other rows are added to
+ *          the output with vector atomics (the output-oriented branch).
+ *  PULL:   each line segment accumulates into a shared-memory Temp over its
+ *          mode interval [T^s, T^e], writes it out as a partial, and a second
+ *          kernel pulls, for each output row, the partials of the segments
+ *          whose interval contains it (the recursive branch).
+ *  AUTO:   PULL when the fiber reuse nnz/dims[mode] exceeds 4 (the paper's
+ *          cost of buffered accumulation) and the largest interval fits in
+ *          shared memory, else ATOMIC. */
+typedef enum alto_variant {
+  ALTO_VARIANT_AUTO = 0,
+  ALTO_VARIANT_ATOMIC = 1,
+  ALTO_VARIANT_PULL = 2
+} alto_variant;
+
+/* Optional device-memory allocator. alloc returns a device pointer aligned to
+ * 256 bytes, or NULL on failure (the library then returns ALTO_ERR_OOM); free
+ * releases it. Both are called from the host thread making the library call,
+ * with that call's stream. NULL allocator = cudaMallocAsync/cudaFreeAsync. */
+typedef struct alto_allocator {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+  void *ctx;
+} alto_allocator;
+
+typedef struct alto_tensor *alto_handle_t;
+
+/* Read-only description of an encoded tensor (alto_query). */
+typedef struct alto_info {
+  int nmodes;
+  int nbits;                          /* sum of bits over modes (Eq. 1 per nonzero) */
+  int key_words;                      /* 64-bit words per position: 1 or 2          */
+  int status;                         /* latched device-side status (alto_status)   */
+  uint64_t nnz;
+  uint64_t nparts;                    /* number of line segments L                  */
+  uint64_t dims[ALTO_MAX_MODES];
+  int bits[ALTO_MAX_MODES];           /* bits of each mode: bit_width(dims[n]-1)    */
+  uint64_t mask_lo[ALTO_MAX_MODES];   /* ALTO bit mask of each mode, low 64 bits    */
+  uint64_t mask_hi[ALTO_MAX_MODES];   /* high 64 bits                               */
+  uint32_t max_interval[ALTO_MAX_MODES]; /* max over segments of T^e - T^s + 1       */
+  uint32_t nhot[ALTO_MAX_MODES];      /* hot rows found per mode                    */
+  double norm_sq;                     /* ||X||^2 = sum of squared values            */
+  size_t device_bytes;                /* device memory held by the handle           */
+} alto_info;
+
+/* Per-mode MTTKRP plan (what the autotuner sets). */
+typedef struct alto_mode_plan {
+  int variant;        /* alto_variant                                             */
+  int cols_per_lane;  /* 4 or 8 factor columns per thread: R/cols_per_lane threads
+                         work on one nonzero ("threads per nonzero")              */
+  int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit             */
+} alto_mode_plan;
+
+/* ---------------------------------------------------------------------------
+ * alto_encode -- Section III-A (linearization and ordering) and Section IV-A
+ * (nnz-balanced line segments and their mode intervals).
+ *
+ *  coords  [nmodes][nnz] uint32, structure of arrays, 0-based; host or device
+ *          memory (host memory is copied in; pin it for an asynchronous copy).
+ *  vals    [nnz] float; host or device memory.
+ *  dims    host array [nmodes] of mode lengths.
+ *  nmodes  1..ALTO_MAX_MODES.
+ *  nnz     number of nonzeros (0 allowed; duplicates are kept, and summed by
+ *          every operation, as in COO).
+ *  alloc   allocator for everything the handle owns, or NULL.
+ *  stream  stream for all device work.
+ *  out     receives the new handle.
+ *
+ * Steps: bits per mode = bit_width(dims[n]-1); bit groups from the least
+ * significant bit, each group holding the modes that still have bits, shortest
+ * mode at the lowest bit; position p = bit-level gather of the coordinates
+ * (PDEP); stable sort of (p, value) by p (ties keep input order); L balanced
+ * segments [floor(l*nnz/L), floor((l+1)*nnz/L)) with per-mode [min, max]
+ * intervals; ||X||^2; the hot rows of every mode (sampled row counts).
+ * The call synchronises the stream before returning (it reads back the
+ * device status word and a few sizes). Coordinates >= dims[n] make it return
+ * ALTO_ERR_COORD_RANGE and free everything. Errors: INVALID_ARG, OOM, CUDA,
+ * UNSUPPORTED (more than 128 index bits), COORD_RANGE.
+ * ------------------------------------------------------------------------- */
+alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_t *dims,
+                        int nmodes, uint64_t nnz, const alto_allocator *alloc, void *stream,
+                        alto_handle_t *out);
+
+/* Release the handle and everything it owns (freed on the stream of the last
+ * call made with it; pending work on that stream is ordered before). NULL ok. */
+void alto_free(alto_handle_t h);
+
+/* Fill *info. Synchronises the handle's last stream to read the latched
+ * device status. */
+alto_status alto_query(alto_handle_t h, alto_info *info);
+
+/* Re-partition into nparts line segments (Section IV-A) and recompute the
+ * mode intervals. Synchronises. Drops cached pull plans. */
+alto_status alto_set_partitions(alto_handle_t h, uint64_t nparts, void *stream);
+
+/* Copy the partition to host memory: starts [nparts+1] (nonzero offsets) and
+ * intervals [nparts][nmodes][2] (closed [T^s, T^e]; an empty segment has
+ * (2^32-1, 0)). Either pointer may be NULL. Synchronises. */
+alto_status alto_copy_partition(alto_handle_t h, uint64_t *starts, uint32_t *intervals);
+
+/* Copy the ordered encoded tensor to device memory: keys [nnz][key_words]
+ * uint64 (low word first) and vals [nnz] float. Either may be NULL. */
+alto_status alto_copy_encoded(alto_handle_t h, uint64_t *keys, float *vals, void *stream);
+
+/* De-linearize every position (EXTRACT with the mode masks, Alg. 3) into
+ * coords [nmodes][nnz] (device) and copy the values in ALTO order to vals
+ * (device, may be NULL). */
+alto_status alto_decode(alto_handle_t h, uint32_t *coords, float *vals, void *stream);
+
+/* Copy mode `mode`'s hot rows (most frequent first) to host memory; at most
+ * cap rows; *count receives how many exist. Synchronises. */
+alto_status alto_copy_hot_rows(alto_handle_t h, int mode, uint32_t *rows, uint32_t cap,
+                               uint32_t *count);
+
+/* Set / read the MTTKRP plan of one mode. alto_get_mode_plan resolves AUTO
+ * for rank R into the concrete choice the next alto_mttkrp would make. */
+alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *plan);
+alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan *plan);
+
+/* ---------------------------------------------------------------------------
+ * alto_mttkrp -- M = X_(mode) (A^(1) (.) ... A^(mode-1) (.) A^(mode+1) ... (.) A^(N))
+ * (Alg. 1 MTTKRP line), computed nonzero by nonzero over the ALTO copy
+ * (Alg. 3) with the conflict resolution of Alg. 4 chosen by the mode plan.
+ *
+ *  mode     0..nmodes-1, the output mode.
+ *  factors  HOST array [nmodes] of DEVICE pointers to row-major dims[m] x R
+ *           matrices of type fdtype; factors[mode] is not read (may be NULL).
+ *  fdtype   ALTO_F32 or ALTO_BF16 (bf16 factors, fp32 arithmetic).
+ *  R        rank: 4, 8, 16, 32 or 64.
+ *  out      DEVICE dims[mode] x R float, overwritten (rows without nonzeros
+ *           become 0).
+ * The first call for a PULL mode builds that mode's row-to-segment lists on
+ * the host (one synchronisation); later calls are asynchronous. fp32 results
+ * differ from the exact sum by rounding only; the summation order of the
+ * ATOMIC variant is not fixed, so bits may vary from run to run.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * ------------------------------------------------------------------------- */
+alto_status alto_mttkrp(alto_handle_t h, int mode, const void *const *factors,
+                        alto_dtype fdtype, int R, float *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * cpals_run -- CP-ALS, Alg. 1: for each iteration and each mode n:
+ * V = Hadamard product of the Grams G_m = A^(m)T A^(m), m != n (fp64);
+ * M = MTTKRP (alto_mttkrp); A^(n) = M V^-1 through a Cholesky factorisation of
+ * V (fp64); lambda = column 2-norms of A^(n); A^(n) /= lambda; after the last
+ * mode the fit 1 - ||X - X_hat|| / ||X|| (fp64).
+ *
+ *  R        rank (4, 8, 16, 32 or 64).
+ *  iters    maximum number of iterations (>= 1).
+ *  factors  HOST array [nmodes] of pointers to dims[m] x R float matrices:
+ *           the initial guess on entry, the normalised result on return.
+ *           All device pointers or all host pointers (host ones are copied
+ *           in and out; pin them for asynchronous copies).
+ *  lambda   [R] double (host or device), the column norms of the last update.
+ *  fits     host [iters] double, the fit after each iteration, or NULL.
+ *  tol      0 runs exactly iters iterations; > 0 stops after the first
+ *           iteration whose fit changed by less than tol.
+ *  iters_done  host int, iterations run, or NULL.
+ * Synchronises when fits, iters_done or host factors are given, and always
+ * reads back the device status at the end. Requires nnz > 0.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, NOT_SPD (V not positive
+ * definite: the factors are left at the last completed update).
+ * ------------------------------------------------------------------------- */
+alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, double *lambda,
+                      double *fits, double tol, int *iters_done, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used to report kernel time
+ * against the memory roofline).
+ *
+ * alto_profile_enable: when on, every kernel the handle launches from
+ * alto_mttkrp and cpals_run is bracketed by a pair of CUDA events recorded on
+ * the launching stream; alto_profile_read synchronises those events and
+ * returns, per kernel kind, the number of launches and their summed device
+ * time in milliseconds (reset != 0 clears the totals afterwards).
+ * alto_kernel_launches: process-wide count of kernels this library has
+ * launched (all handles, all kinds; memsets and copies are not counted).
+ * ------------------------------------------------------------------------- */
+typedef enum alto_prof_kind {
+  ALTO_PROF_MTTKRP = 0,       /* the segment kernel of Alg. 3/4             */
+  ALTO_PROF_PULL_REDUCE = 1,  /* the pull-based reduction of Alg. 4         */
+  ALTO_PROF_ZERO = 2,         /* zeroing of the output (ATOMIC variant)      */
+  ALTO_PROF_GRAM = 3,         /* A^T A of a factor or of M                  */
+  ALTO_PROF_SOLVE = 4,        /* fp64 Hadamard / Cholesky / lambda / fit    */
+  ALTO_PROF_RMUL = 5,         /* A^(n) = M V^-1 diag(1/lambda)              */
+  ALTO_PROF_KINDS = 6
+} alto_prof_kind;
+
+typedef struct alto_profile {
+  uint64_t launches[ALTO_PROF_KINDS];
+  double ms[ALTO_PROF_KINDS];
+} alto_profile;
+
+alto_status alto_profile_enable(alto_handle_t h, int on);
+alto_status alto_profile_read(alto_handle_t h, alto_profile *out, int reset);
+uint64_t alto_kernel_launches(void);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *alto_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int alto_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALTO_H_ */

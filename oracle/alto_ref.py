@@ -322,6 +322,27 @@ def cp_fit(normX2: float, lam: np.ndarray, factors: Sequence[np.ndarray],
     return 1.0 - np.sqrt(resid2) / np.sqrt(normX2)
 
 
+def cp_als_mode_update(coords: np.ndarray, vals: np.ndarray, A: List[np.ndarray], n: int,
+                       mttkrp_fn=None) -> Tuple[np.ndarray, np.ndarray]:
+    """One pass of the inner loop of Alg. 1 for mode n, updating A[n] in place:
+    V = Hadamard product of the other Grams, M = MTTKRP, A^(n) = M V^dagger,
+    lambda = column norms, A^(n) normalised. Returns (M, lambda)."""
+    if mttkrp_fn is None:
+        mttkrp_fn = mttkrp
+    N = len(A)
+    R = A[0].shape[1]
+    V = np.ones((R, R))
+    for m in range(N):
+        if m != n:
+            V *= A[m].T @ A[m]
+    M = mttkrp_fn(coords, vals, A, n)
+    An = _solve_spd_or_pinv(V, M)
+    lam = np.sqrt(np.sum(An * An, axis=0))
+    scale = np.where(lam > 0, 1.0 / np.where(lam > 0, lam, 1.0), 1.0)
+    A[n] = An * scale
+    return M, lam
+
+
 @dataclasses.dataclass
 class CPResult:
     factors: List[np.ndarray]
@@ -346,15 +367,7 @@ def cp_als(coords: np.ndarray, vals: np.ndarray, dims: Sequence[int],
     for _ in range(iters):
         M = None
         for n in range(N):
-            V = np.ones((R, R))
-            for m in range(N):
-                if m != n:
-                    V *= A[m].T @ A[m]
-            M = mttkrp_fn(coords, vals, A, n)
-            An = _solve_spd_or_pinv(V, M)
-            lam = np.sqrt(np.sum(An * An, axis=0))
-            scale = np.where(lam > 0, 1.0 / np.where(lam > 0, lam, 1.0), 1.0)
-            A[n] = An * scale
+            M, lam = cp_als_mode_update(coords, vals, A, n, mttkrp_fn)
         fit = cp_fit(normX2, lam, A, M)
         fits.append(fit)
         if tol > 0 and prev is not None and abs(fit - prev) < tol:

@@ -1,0 +1,310 @@
+"""Python binding of libalto (ALTO sparse tensors on GB300, sm_103a).
+
+Thin ctypes marshalling over the C ABI in include/alto.h: every step of the
+encode, MTTKRP and CP-ALS path runs in the library's CUDA kernels. PyTorch is
+used only for device memory and streams. There is no CPU fallback: if the
+compiled library is missing, ``lib()`` raises.
+
+The module-level functions carry the C names (``alto_encode``,
+``alto_mttkrp``, ``cpals_run``, ...); ``AltoTensor`` wraps a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libalto.so")
+
+ALTO_MAX_MODES = 8
+ALTO_MAX_HOT = 4096
+ALTO_F32, ALTO_BF16 = 0, 1
+VARIANT_AUTO, VARIANT_ATOMIC, VARIANT_PULL = 0, 1, 2
+
+STATUS_NAMES = {0: "ALTO_OK", -1: "ALTO_ERR_INVALID_ARG", -2: "ALTO_ERR_OOM", -3: "ALTO_ERR_CUDA",
+                -4: "ALTO_ERR_UNSUPPORTED", -5: "ALTO_ERR_COORD_RANGE", -6: "ALTO_ERR_NOT_SPD",
+                -7: "ALTO_ERR_TIMEOUT"}
+
+
+class AltoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class alto_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                           ctypes.c_void_p)),
+                ("free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                          ctypes.c_void_p)),
+                ("ctx", ctypes.c_void_p)]
+
+
+class alto_info(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int), ("nbits", ctypes.c_int), ("key_words", ctypes.c_int),
+                ("status", ctypes.c_int), ("nnz", ctypes.c_uint64), ("nparts", ctypes.c_uint64),
+                ("dims", ctypes.c_uint64 * ALTO_MAX_MODES), ("bits", ctypes.c_int * ALTO_MAX_MODES),
+                ("mask_lo", ctypes.c_uint64 * ALTO_MAX_MODES),
+                ("mask_hi", ctypes.c_uint64 * ALTO_MAX_MODES),
+                ("max_interval", ctypes.c_uint32 * ALTO_MAX_MODES),
+                ("nhot", ctypes.c_uint32 * ALTO_MAX_MODES), ("norm_sq", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+PROF_KINDS = ("mttkrp", "pull_reduce", "zero", "gram", "solve", "rmul")
+
+
+class alto_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * len(PROF_KINDS)),
+                ("ms", ctypes.c_double * len(PROF_KINDS))]
+
+
+class alto_mode_plan(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("cols_per_lane", ctypes.c_int),
+                ("hot_rows", ctypes.c_int)]
+
+
+# Exported symbols and their ctypes signatures (mirrors include/alto.h).
+_vp, _u64, _i32, _u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+SIGNATURES = {
+    "alto_encode": ([_vp, _vp, _vp, _i32, _u64, _vp, _vp, _vp], _i32),
+    "alto_free": ([_vp], None),
+    "alto_query": ([_vp, ctypes.POINTER(alto_info)], _i32),
+    "alto_set_partitions": ([_vp, _u64, _vp], _i32),
+    "alto_copy_partition": ([_vp, _vp, _vp], _i32),
+    "alto_copy_encoded": ([_vp, _vp, _vp, _vp], _i32),
+    "alto_decode": ([_vp, _vp, _vp, _vp], _i32),
+    "alto_copy_hot_rows": ([_vp, _i32, _vp, _u32, ctypes.POINTER(_u32)], _i32),
+    "alto_set_mode_plan": ([_vp, _i32, ctypes.POINTER(alto_mode_plan)], _i32),
+    "alto_get_mode_plan": ([_vp, _i32, _i32, ctypes.POINTER(alto_mode_plan)], _i32),
+    "alto_mttkrp": ([_vp, _i32, _vp, _i32, _i32, _vp, _vp], _i32),
+    "cpals_run": ([_vp, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_i32), _vp],
+                  _i32),
+    "alto_profile_enable": ([_vp, _i32], _i32),
+    "alto_profile_read": ([_vp, ctypes.POINTER(alto_profile), _i32], _i32),
+    "alto_kernel_launches": ([], _u64),
+    "alto_last_error": ([], ctypes.c_char_p),
+    "alto_version": ([], _i32),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def alto_kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().alto_kernel_launches())
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree libalto.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libalto.so not built ({LIB_PATH}); run "
+                               "paper_2403_06348_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        msg = lib().alto_last_error()
+        raise AltoError(status, msg.decode() if msg else "")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points (argument marshalling only)
+# ---------------------------------------------------------------------------
+
+def alto_encode(coords, vals, dims: Sequence[int], stream=None, allocator=None) -> "AltoTensor":
+    """Encode a COO tensor. ``coords`` is [nmodes, nnz] uint32/int32 and ``vals``
+    [nnz] float32, each a CUDA tensor or a (host) numpy array / CPU tensor."""
+    keep = []
+
+    def prep(x, np_dtype):
+        if isinstance(x, np.ndarray):
+            a = np.ascontiguousarray(x, dtype=np_dtype)
+            keep.append(a)
+            return a.ctypes.data
+        torch = _torch()
+        if x.device.type == "cpu":
+            a = np.ascontiguousarray(x.numpy(), dtype=np_dtype)
+            keep.append(a)
+            return a.ctypes.data
+        x = x.contiguous()
+        keep.append(x)
+        return x.data_ptr()
+
+    nmodes = len(dims)
+    if hasattr(coords, "shape") and coords.shape[0] != nmodes:
+        raise ValueError("coords must be [nmodes, nnz]")
+    nnz = int(coords.shape[1]) if nmodes else 0
+    cp = prep(coords, np.uint32)
+    vp = prep(vals, np.float32)
+    dims_a = (ctypes.c_uint64 * nmodes)(*[int(d) for d in dims])
+    h = ctypes.c_void_p()
+    al = ctypes.byref(allocator) if allocator is not None else None
+    _check(lib().alto_encode(cp, vp, dims_a, nmodes, nnz, al, _stream_ptr(stream), ctypes.byref(h)))
+    return AltoTensor(h, tuple(int(d) for d in dims), nnz, allocator)
+
+
+def alto_mttkrp(t: "AltoTensor", mode: int, factors, R: int, out, dtype: int = ALTO_F32,
+                stream=None) -> None:
+    arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
+    _check(lib().alto_mttkrp(t.handle, int(mode), arr, int(dtype), int(R), _ptr(out),
+                             _stream_ptr(stream)))
+
+
+def cpals_run(t: "AltoTensor", R: int, iters: int, factors, lam, fits: Optional[np.ndarray] = None,
+              tol: float = 0.0, stream=None) -> int:
+    arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
+    done = ctypes.c_int(0)
+    _check(lib().cpals_run(t.handle, int(R), int(iters), arr, _ptr(lam),
+                           _ptr(fits) if fits is not None else None, float(tol),
+                           ctypes.byref(done), _stream_ptr(stream)))
+    return int(done.value)
+
+
+# ---------------------------------------------------------------------------
+# handle wrapper
+# ---------------------------------------------------------------------------
+
+class AltoTensor:
+    """An encoded tensor on the current CUDA device."""
+
+    def __init__(self, handle: ctypes.c_void_p, dims: Tuple[int, ...], nnz: int, allocator=None):
+        self.handle = handle
+        self.dims = dims
+        self.nnz = nnz
+        self._allocator = allocator  # keep the callbacks alive
+
+    @property
+    def nmodes(self) -> int:
+        return len(self.dims)
+
+    def free(self) -> None:
+        if self.handle:
+            lib().alto_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def query(self) -> alto_info:
+        info = alto_info()
+        _check(lib().alto_query(self.handle, ctypes.byref(info)))
+        return info
+
+    def profile_enable(self, on: bool = True) -> None:
+        _check(lib().alto_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self, reset: bool = False) -> dict:
+        p = alto_profile()
+        _check(lib().alto_profile_read(self.handle, ctypes.byref(p), 1 if reset else 0))
+        return {k: (int(p.launches[i]), float(p.ms[i])) for i, k in enumerate(PROF_KINDS)}
+
+    def set_partitions(self, nparts: int, stream=None) -> None:
+        _check(lib().alto_set_partitions(self.handle, int(nparts), _stream_ptr(stream)))
+
+    def partition(self) -> Tuple[np.ndarray, np.ndarray]:
+        info = self.query()
+        L = int(info.nparts)
+        starts = np.empty(L + 1, dtype=np.uint64)
+        iv = np.empty((L, self.nmodes, 2), dtype=np.uint32)
+        _check(lib().alto_copy_partition(self.handle, starts.ctypes.data, iv.ctypes.data))
+        return starts, iv
+
+    def encoded(self, stream=None):
+        torch = _torch()
+        info = self.query()
+        kw = int(info.key_words)
+        keys = torch.empty((self.nnz, kw), dtype=torch.int64, device="cuda")
+        vals = torch.empty(self.nnz, dtype=torch.float32, device="cuda")
+        _check(lib().alto_copy_encoded(self.handle, _ptr(keys), _ptr(vals), _stream_ptr(stream)))
+        return keys, vals
+
+    def decode(self, stream=None):
+        torch = _torch()
+        coords = torch.empty((self.nmodes, self.nnz), dtype=torch.int32, device="cuda")
+        vals = torch.empty(self.nnz, dtype=torch.float32, device="cuda")
+        _check(lib().alto_decode(self.handle, _ptr(coords), _ptr(vals), _stream_ptr(stream)))
+        return coords, vals
+
+    def hot_rows(self, mode: int) -> np.ndarray:
+        buf = np.empty(ALTO_MAX_HOT, dtype=np.uint32)
+        cnt = ctypes.c_uint32(0)
+        _check(lib().alto_copy_hot_rows(self.handle, int(mode), buf.ctypes.data, ALTO_MAX_HOT,
+                                        ctypes.byref(cnt)))
+        return buf[: cnt.value].copy()
+
+    def set_mode_plan(self, mode: int, variant: int = VARIANT_AUTO, cols_per_lane: int = 0,
+                      hot_rows: int = -1) -> None:
+        p = alto_mode_plan(int(variant), int(cols_per_lane), int(hot_rows))
+        _check(lib().alto_set_mode_plan(self.handle, int(mode), ctypes.byref(p)))
+
+    def get_mode_plan(self, mode: int, R: int) -> Tuple[int, int, int]:
+        p = alto_mode_plan()
+        _check(lib().alto_get_mode_plan(self.handle, int(mode), int(R), ctypes.byref(p)))
+        return int(p.variant), int(p.cols_per_lane), int(p.hot_rows)
+
+    def mttkrp(self, mode: int, factors, R: Optional[int] = None, out=None, dtype=None,
+               stream=None):
+        torch = _torch()
+        R = int(R if R is not None else factors[(mode + 1) % self.nmodes].shape[1])
+        code = ALTO_F32
+        for m, f in enumerate(factors):
+            if m != mode and f is not None and f.dtype == torch.bfloat16:
+                code = ALTO_BF16
+        if dtype is not None:
+            code = dtype
+        if out is None:
+            out = torch.empty((self.dims[mode], R), dtype=torch.float32, device="cuda")
+        alto_mttkrp(self, mode, factors, R, out, code, stream)
+        return out
+
+    def cpals(self, R: int, iters: int, factors, tol: float = 0.0, stream=None):
+        """Run CP-ALS in place on ``factors`` (CUDA float32 tensors or numpy
+        float32 arrays). Returns (lambda float64 numpy [R], fits list)."""
+        torch = _torch()
+        on_dev = not isinstance(factors[0], np.ndarray)
+        lam = torch.empty(R, dtype=torch.float64, device="cuda") if on_dev else np.empty(R)
+        fits = np.zeros(iters, dtype=np.float64)
+        done = cpals_run(self, R, iters, factors, lam, fits, tol, stream)
+        lam_np = lam.cpu().numpy() if on_dev else lam
+        return lam_np, fits[:done].tolist()

@@ -1,0 +1,1008 @@
+// C ABI of the ALTO library: handle management, the bit plan of Section III-A,
+// and the orchestration of the encode, MTTKRP and CP-ALS kernels.
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "alto_internal.cuh"
+#include "cpals.cuh"
+#include "encode.cuh"
+#include "mttkrp.cuh"
+
+using namespace alto;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void alto::note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct ProfEvt {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+alto_status fail(alto_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail(ALTO_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct PullPlan {
+  bool valid = false;
+  uint64_t *part_off = nullptr;  // [L]
+  uint64_t *row_ptr = nullptr;   // [I+1]
+  uint64_t *prow = nullptr;      // [entries]
+  uint64_t total_rows = 0;
+  uint64_t entries = 0;
+};
+
+struct HotTable {
+  int nslots = -1;
+  int hbits = 0;
+  uint64_t *htab = nullptr;
+};
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct alto_tensor {
+  int N = 0, nbits = 0, kw = 1;
+  uint64_t M = 0;
+  uint64_t dims[kMaxModes] = {};
+  int bits[kMaxModes] = {};
+  uint64_t mask_lo[kMaxModes] = {}, mask_hi[kMaxModes] = {};
+  DecodePlan dp{};
+  alto_allocator alloc{};
+  bool user_alloc = false;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 1;
+  size_t bytes_held = 0;
+  // device state
+  uint64_t *keys = nullptr;
+  float *vals = nullptr;
+  uint64_t *dims_dev = nullptr;
+  uint64_t L = 0;
+  uint32_t *intervals = nullptr;
+  uint32_t *max_len_dev = nullptr;
+  uint32_t *status_dev = nullptr;
+  double *norm_sq_dev = nullptr;
+  uint32_t *hot_rows[kMaxModes] = {};
+  uint32_t *nhot_dev = nullptr;
+  // host mirrors
+  uint32_t max_interval[kMaxModes] = {};
+  uint32_t nhot[kMaxModes] = {};
+  std::vector<uint32_t> hot_host[kMaxModes];
+  double norm_sq = 0.0;
+  std::vector<uint32_t> intervals_host;
+  bool intervals_host_valid = false;
+  // plans and caches
+  alto_mode_plan plan[kMaxModes];
+  HotTable hot_tab[kMaxModes];
+  PullPlan pull[kMaxModes];
+  Buf partials;
+  // instrumentation
+  bool prof_on = false;
+  std::vector<ProfEvt> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[ALTO_PROF_KINDS] = {};
+  uint64_t prof_n[ALTO_PROF_KINDS] = {};
+};
+
+namespace {
+
+void *dalloc(alto_tensor *h, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (h->user_alloc) {
+    p = h->alloc.alloc(bytes, (void *)s, h->alloc.ctx);
+  } else if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->bytes_held += bytes;
+  return p;
+}
+
+void dfree(alto_tensor *h, void *p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (h->user_alloc)
+    h->alloc.free(p, bytes, (void *)s, h->alloc.ctx);
+  else
+    cudaFreeAsync(p, s);
+  h->bytes_held -= bytes;
+}
+
+cudaEvent_t prof_event(alto_tensor *h) {
+  if (!h->prof_pool.empty()) {
+    cudaEvent_t e = h->prof_pool.back();
+    h->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Brackets the kernels launched in its scope with CUDA events on stream s.
+struct ProfScope {
+  alto_tensor *h;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(alto_tensor *h_, int kind_, cudaStream_t s_) : h(h_), kind(kind_), s(s_) {
+    if (h->prof_on && (a = prof_event(h)) != nullptr) cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(h);
+    if (!b) {
+      h->prof_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    h->prof_pending.push_back(ProfEvt{kind, a, b});
+  }
+};
+
+template <typename T>
+alto_status alloc_n(alto_tensor *h, T **p, size_t n, cudaStream_t s, const char *what) {
+  *p = static_cast<T *>(dalloc(h, n * sizeof(T), s));
+  if (!*p) return fail(ALTO_ERR_OOM, "allocation of %zu bytes for %s failed", n * sizeof(T), what);
+  return ALTO_OK;
+}
+
+int mode_bits(uint64_t I) {
+  if (I <= 1) return 0;
+  return 64 - __builtin_clzll(I - 1);
+}
+
+// Section III-A bit plan: groups from the LSB, shortest mode lowest.
+alto_status build_bit_plan(alto_tensor *h) {
+  const int N = h->N;
+  int order[kMaxModes];
+  for (int n = 0; n < N; ++n) {
+    order[n] = n;
+    h->bits[n] = mode_bits(h->dims[n]);
+  }
+  std::stable_sort(order, order + N, [&](int a, int b) { return h->dims[a] < h->dims[b]; });
+  int pos[kMaxModes][32];
+  int p = 0, maxb = 0;
+  for (int n = 0; n < N; ++n) maxb = std::max(maxb, h->bits[n]);
+  for (int g = 0; g < maxb; ++g)
+    for (int k = 0; k < N; ++k) {
+      const int n = order[k];
+      if (h->bits[n] > g) pos[n][g] = p++;
+    }
+  h->nbits = p;
+  if (p > 128) return fail(ALTO_ERR_UNSUPPORTED, "%d index bits exceed 128", p);
+  h->kw = p <= 64 ? 1 : 2;
+  DecodePlan &dp = h->dp;
+  memset(&dp, 0, sizeof(dp));
+  dp.nmodes = N;
+  dp.kw = h->kw;
+  for (int n = 0; n < N; ++n) {
+    h->mask_lo[n] = h->mask_hi[n] = 0;
+    for (int g = 0; g < h->bits[n]; ++g) {
+      if (pos[n][g] < 64)
+        h->mask_lo[n] |= 1ull << pos[n][g];
+      else
+        h->mask_hi[n] |= 1ull << (pos[n][g] - 64);
+    }
+    // split the mode's positions into arithmetic runs inside 64-bit windows
+    int nr = 0, g = 0;
+    while (g < h->bits[n]) {
+      const int start = pos[n][g];
+      int stride = 1, cnt = 1;
+      if (g + 1 < h->bits[n]) {
+        const int d = pos[n][g + 1] - start;
+        if (d <= 8 && pos[n][g + 1] - start < 64) {
+          stride = d;
+          cnt = 2;
+          while (g + cnt < h->bits[n] && pos[n][g + cnt] - pos[n][g + cnt - 1] == stride &&
+                 pos[n][g + cnt] - start < 64)
+            ++cnt;
+        }
+      }
+      if (nr >= kMaxRuns) return fail(ALTO_ERR_UNSUPPORTED, "bit plan needs too many runs");
+      dp.runs[n][nr].shift = (uint8_t)start;
+      dp.runs[n][nr].stride = (uint8_t)stride;
+      dp.runs[n][nr].count = (uint8_t)cnt;
+      dp.runs[n][nr].outshift = (uint8_t)g;
+      ++nr;
+      g += cnt;
+    }
+    dp.nruns[n] = nr;
+  }
+  return ALTO_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+uint64_t default_parts(uint64_t M, int num_sms) {
+  if (M == 0) return 1;
+  uint64_t L = (M + 16383) / 16384;
+  const uint64_t want = std::min<uint64_t>((M + 1023) / 1024, 2ull * (uint64_t)num_sms);
+  return std::max<uint64_t>(std::max<uint64_t>(L, want), 1);
+}
+
+void free_pull(alto_tensor *h, int n, cudaStream_t s) {
+  PullPlan &pp = h->pull[n];
+  if (pp.part_off) dfree(h, pp.part_off, h->L * sizeof(uint64_t), s);
+  if (pp.row_ptr) dfree(h, pp.row_ptr, (h->dims[n] + 1) * sizeof(uint64_t), s);
+  if (pp.prow) dfree(h, pp.prow, pp.entries * sizeof(uint64_t), s);
+  pp = PullPlan();
+}
+
+void free_hot(alto_tensor *h, int n, cudaStream_t s) {
+  HotTable &ht = h->hot_tab[n];
+  if (ht.htab) dfree(h, ht.htab, ((size_t)1 << ht.hbits) * sizeof(uint64_t), s);
+  ht = HotTable();
+}
+
+alto_status run_partition(alto_tensor *h, uint64_t L, cudaStream_t s) {
+  if (h->intervals) dfree(h, h->intervals, h->L * h->N * 2 * sizeof(uint32_t), s);
+  h->intervals = nullptr;
+  h->L = L;
+  alto_status st = alloc_n(h, &h->intervals, (size_t)L * h->N * 2, s, "intervals");
+  if (st != ALTO_OK) return st;
+  CUDA_TRY(cudaMemsetAsync(h->max_len_dev, 0, kMaxModes * sizeof(uint32_t), s));
+  if (h->M == 0) {
+    CUDA_TRY(cudaMemsetAsync(h->intervals, 0xFF, (size_t)L * h->N * 2 * sizeof(uint32_t), s));
+    // empty interval convention: (2^32-1, 0)
+    std::vector<uint32_t> iv((size_t)L * h->N * 2);
+    for (size_t i = 0; i < iv.size(); i += 2) {
+      iv[i] = kEmptyRow;
+      iv[i + 1] = 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->intervals, iv.data(), iv.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  } else {
+    CUDA_TRY(launch_partition(h->dp, h->keys, h->M, L, h->intervals, h->max_len_dev, h->num_sms, s));
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->max_interval, h->max_len_dev, kMaxModes * sizeof(uint32_t),
+                           cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->intervals_host_valid = false;
+  for (int n = 0; n < h->N; ++n) free_pull(h, n, s);
+  return ALTO_OK;
+}
+
+alto_status ensure_intervals_host(alto_tensor *h, cudaStream_t s) {
+  if (h->intervals_host_valid) return ALTO_OK;
+  h->intervals_host.resize((size_t)h->L * h->N * 2);
+  CUDA_TRY(cudaMemcpyAsync(h->intervals_host.data(), h->intervals,
+                           h->intervals_host.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->intervals_host_valid = true;
+  return ALTO_OK;
+}
+
+// Row -> segment lists of the pull reduction (Alg. 4), built on the host from
+// the mode intervals; every row lists its partial rows in segment order.
+alto_status ensure_pull(alto_tensor *h, int n, cudaStream_t s) {
+  PullPlan &pp = h->pull[n];
+  if (pp.valid) return ALTO_OK;
+  alto_status st = ensure_intervals_host(h, s);
+  if (st != ALTO_OK) return st;
+  const uint64_t L = h->L, I = h->dims[n];
+  const int N = h->N;
+  std::vector<uint64_t> part_off(L);
+  std::vector<uint64_t> cnt(I + 1, 0);
+  uint64_t total = 0;
+  for (uint64_t l = 0; l < L; ++l) {
+    const uint32_t a = h->intervals_host[(l * N + n) * 2], b = h->intervals_host[(l * N + n) * 2 + 1];
+    part_off[l] = total;
+    if (a <= b) {
+      total += (uint64_t)(b - a) + 1;
+      for (uint64_t r = a; r <= b; ++r) cnt[r + 1]++;
+    }
+  }
+  for (uint64_t i = 0; i < I; ++i) cnt[i + 1] += cnt[i];
+  std::vector<uint64_t> fillpos(cnt.begin(), cnt.end() - 1);
+  std::vector<uint64_t> prow(total);
+  for (uint64_t l = 0; l < L; ++l) {
+    const uint32_t a = h->intervals_host[(l * N + n) * 2], b = h->intervals_host[(l * N + n) * 2 + 1];
+    if (a <= b)
+      for (uint64_t r = a; r <= b; ++r) prow[fillpos[r]++] = part_off[l] + (r - a);
+  }
+  pp.total_rows = total;
+  pp.entries = total;
+  if ((st = alloc_n(h, &pp.part_off, L, s, "pull offsets")) != ALTO_OK) return st;
+  if ((st = alloc_n(h, &pp.row_ptr, I + 1, s, "pull row pointers")) != ALTO_OK) return st;
+  if ((st = alloc_n(h, &pp.prow, std::max<uint64_t>(total, 1), s, "pull lists")) != ALTO_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(pp.part_off, part_off.data(), L * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(pp.row_ptr, cnt.data(), (I + 1) * 8, cudaMemcpyHostToDevice, s));
+  if (total) CUDA_TRY(cudaMemcpyAsync(pp.prow, prow.data(), total * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
+  pp.valid = true;
+  return ALTO_OK;
+}
+
+// Hash table of the first nslots hot rows of mode n (open addressing).
+alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) {
+  HotTable &ht = h->hot_tab[n];
+  if (ht.nslots == nslots && ht.htab) return ALTO_OK;
+  free_hot(h, n, s);
+  int hbits = 1;
+  while ((1 << hbits) < 2 * std::max(nslots, 1)) ++hbits;
+  const size_t hsize = (size_t)1 << hbits;
+  std::vector<uint64_t> tab(hsize, ~0ull);
+  for (int sl = 0; sl < nslots; ++sl) {
+    const uint32_t row = h->hot_host[n][sl];
+    uint32_t k = (row * 0x9E3779B1u) >> (32 - hbits);
+    while ((uint32_t)tab[k] != kEmptyRow) k = (k + 1) & (uint32_t)(hsize - 1);
+    tab[k] = ((uint64_t)sl << 32) | row;
+  }
+  alto_status st = alloc_n(h, &ht.htab, hsize, s, "hot table");
+  if (st != ALTO_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(ht.htab, tab.data(), hsize * 8, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  ht.nslots = nslots;
+  ht.hbits = hbits;
+  return ALTO_OK;
+}
+
+bool rank_ok(int R) { return R == 4 || R == 8 || R == 16 || R == 32 || R == 64; }
+
+// Shared memory budget per CTA for the staged tables: two CTAs per SM.
+size_t stage_budget() { return std::min<size_t>(mttkrp_smem_limit(), 110 * 1024); }
+
+int hot_slots_that_fit(int R, int want) {
+  const size_t budget = stage_budget();
+  int k = want;
+  while (k > 0) {
+    int hbits = 1;
+    while ((1 << hbits) < 2 * k) ++hbits;
+    if (mttkrp_smem_bytes(false, R, k, hbits, 0) <= budget) break;
+    k = k * 7 / 8;
+  }
+  return std::max(k, 0);
+}
+
+alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
+  alto_mode_plan p = h->plan[mode];
+  if (p.cols_per_lane != 4 && p.cols_per_lane != 8) p.cols_per_lane = (R % 8 == 0) ? 8 : 4;
+  if (R % p.cols_per_lane) p.cols_per_lane = 4;
+  const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
+  const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
+  if (p.variant == ALTO_VARIANT_AUTO) {
+    const double reuse = (double)h->M / (double)h->dims[mode];
+    p.variant = (reuse > 4.0 && pull_fits && pull_smem <= stage_budget()) ? ALTO_VARIANT_PULL
+                                                                           : ALTO_VARIANT_ATOMIC;
+  }
+  if (p.variant == ALTO_VARIANT_PULL && !pull_fits)
+    return fail(ALTO_ERR_UNSUPPORTED, "mode %d: interval of %u rows does not fit shared memory",
+                mode, h->max_interval[mode]);
+  if (p.variant == ALTO_VARIANT_ATOMIC) {
+    const int avail = (int)h->nhot[mode];
+    const int want = (p.hot_rows < 0 || p.hot_rows > avail) ? avail : p.hot_rows;
+    p.hot_rows = hot_slots_that_fit(R, want);
+  } else {
+    p.hot_rows = 0;
+  }
+  *out = p;
+  return ALTO_OK;
+}
+
+alto_status check_handle(alto_tensor *h) {
+  if (!h) return fail(ALTO_ERR_INVALID_ARG, "null handle");
+  return ALTO_OK;
+}
+
+alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bool bf16, int R,
+                        float *out, cudaStream_t s) {
+  alto_mode_plan p;
+  alto_status st = resolve_plan(h, mode, R, &p);
+  if (st != ALTO_OK) return st;
+  const uint64_t I = h->dims[mode];
+  MttkrpArgs a{};
+  a.dp = h->dp;
+  a.keys = h->keys;
+  a.vals = h->vals;
+  a.nnz = h->M;
+  a.L = h->L;
+  a.intervals = h->intervals;
+  for (int m = 0; m < h->N; ++m) a.factors[m] = factors[m];
+  a.out = out;
+  a.mode = mode;
+  a.R = R;
+  if (h->M == 0) {
+    CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
+    return ALTO_OK;
+  }
+  if (p.variant == ALTO_VARIANT_PULL) {
+    if ((st = ensure_pull(h, mode, s)) != ALTO_OK) return st;
+    const PullPlan &pp = h->pull[mode];
+    const size_t need = pp.total_rows * (size_t)R * sizeof(float);
+    if (h->partials.bytes < need) {
+      dfree(h, h->partials.p, h->partials.bytes, s);
+      h->partials.p = dalloc(h, need, s);
+      h->partials.bytes = h->partials.p ? need : 0;
+      if (!h->partials.p) return fail(ALTO_ERR_OOM, "pull partials of %zu bytes", need);
+    }
+    a.partials = static_cast<float *>(h->partials.p);
+    a.part_off = pp.part_off;
+    const size_t smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
+    {
+      ProfScope ps(h, ALTO_PROF_MTTKRP, s);
+      CUDA_TRY(launch_mttkrp(a, p.cols_per_lane, bf16, true, smem, h->num_sms, s));
+    }
+    {
+      ProfScope ps(h, ALTO_PROF_PULL_REDUCE, s);
+      CUDA_TRY(launch_pull_reduce(a.partials, pp.row_ptr, pp.prow, I, R, out, h->num_sms, s));
+    }
+  } else {
+    if ((st = ensure_hot_table(h, mode, p.hot_rows, s)) != ALTO_OK) return st;
+    const HotTable &ht = h->hot_tab[mode];
+    a.htab = ht.htab;
+    a.slot_rows = h->hot_rows[mode];
+    a.hbits = ht.hbits;
+    a.nslots = ht.nslots;
+    const size_t smem = mttkrp_smem_bytes(false, R, ht.nslots, ht.hbits, 0);
+    {
+      ProfScope ps(h, ALTO_PROF_ZERO, s);
+      CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
+    }
+    {
+      ProfScope ps(h, ALTO_PROF_MTTKRP, s);
+      CUDA_TRY(launch_mttkrp(a, p.cols_per_lane, bf16, false, smem, h->num_sms, s));
+    }
+  }
+  return ALTO_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *alto_last_error(void) { return g_last_error.c_str(); }
+
+int alto_version(void) { return 100; }
+
+alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_t *dims, int nmodes,
+                        uint64_t nnz, const alto_allocator *alloc, void *stream, alto_handle_t *out) {
+  g_last_error.clear();
+  if (!out) return fail(ALTO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nmodes < 1 || nmodes > ALTO_MAX_MODES)
+    return fail(ALTO_ERR_INVALID_ARG, "nmodes %d not in 1..%d", nmodes, ALTO_MAX_MODES);
+  if (!dims) return fail(ALTO_ERR_INVALID_ARG, "dims is NULL");
+  for (int n = 0; n < nmodes; ++n)
+    if (dims[n] < 1 || dims[n] > 0xFFFFFFFFull)
+      return fail(ALTO_ERR_INVALID_ARG, "dims[%d] = %llu not in [1, 2^32)", n,
+                  (unsigned long long)dims[n]);
+  if (nnz >= 0xFFFFFFFFull) return fail(ALTO_ERR_UNSUPPORTED, "nnz must be < 2^32");
+  if (nnz > 0 && (!coords || !vals)) return fail(ALTO_ERR_INVALID_ARG, "coords/vals NULL");
+  if (alloc && (!alloc->alloc || !alloc->free))
+    return fail(ALTO_ERR_INVALID_ARG, "allocator without alloc/free");
+
+  alto_tensor *h = new alto_tensor();
+  h->N = nmodes;
+  h->M = nnz;
+  for (int n = 0; n < nmodes; ++n) h->dims[n] = dims[n];
+  if (alloc) {
+    h->alloc = *alloc;
+    h->user_alloc = true;
+  }
+  for (int n = 0; n < kMaxModes; ++n) {
+    h->plan[n].variant = ALTO_VARIANT_AUTO;
+    h->plan[n].cols_per_lane = 0;
+    h->plan[n].hot_rows = -1;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  alto_status st = build_bit_plan(h);
+  if (st != ALTO_OK) {
+    delete h;
+    return st;
+  }
+  auto bail = [&](alto_status code) {
+    alto_free(h);
+    return code;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(ALTO_ERR_CUDA, "no CUDA device");
+  }
+  const uint64_t M = nnz;
+  const int N = nmodes, kw = h->kw;
+
+  // resident state
+  if ((st = alloc_n(h, &h->dims_dev, kMaxModes, s, "dims")) != ALTO_OK) return bail(st);
+  if ((st = alloc_n(h, &h->status_dev, 4, s, "status")) != ALTO_OK) return bail(st);
+  if ((st = alloc_n(h, &h->norm_sq_dev, 1, s, "norm")) != ALTO_OK) return bail(st);
+  if ((st = alloc_n(h, &h->max_len_dev, kMaxModes, s, "max interval")) != ALTO_OK) return bail(st);
+  if ((st = alloc_n(h, &h->nhot_dev, kMaxModes, s, "hot counts")) != ALTO_OK) return bail(st);
+  for (int n = 0; n < N; ++n)
+    if ((st = alloc_n(h, &h->hot_rows[n], ALTO_MAX_HOT, s, "hot rows")) != ALTO_OK) return bail(st);
+  uint64_t dims_pad[kMaxModes] = {};
+  for (int n = 0; n < N; ++n) dims_pad[n] = dims[n];
+  if (cudaMemcpyAsync(h->dims_dev, dims_pad, sizeof(dims_pad), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(h->status_dev, 0, 4 * sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(h->norm_sq_dev, 0, sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(h->nhot_dev, 0, kMaxModes * sizeof(uint32_t), s) != cudaSuccess)
+    return bail(fail(ALTO_ERR_CUDA, "initialising handle state"));
+
+  // temporaries
+  uint32_t *coords_d = const_cast<uint32_t *>(coords);
+  float *vals_d = const_cast<float *>(vals);
+  bool own_coords = false, own_vals = false;
+  uint64_t *kbuf[2] = {nullptr, nullptr};
+  float *vbuf[2] = {nullptr, nullptr};
+  uint32_t *table = nullptr, *table_scan = nullptr, *block_sums = nullptr;
+  uint32_t *counts = nullptr, *hot_scratch = nullptr;
+  uint32_t **counts_ptrs_dev = nullptr;
+  uint64_t *hot_list = nullptr;
+  uint64_t sum_dims = 0;
+  for (int n = 0; n < N; ++n) sum_dims += dims[n];
+  const size_t entries = sort_table_entries(M);
+  const size_t nblocks = sort_scan_blocks(M);
+  auto cleanup = [&]() {
+    if (own_coords) dfree(h, coords_d, (size_t)N * M * 4, s);
+    if (own_vals) dfree(h, vals_d, M * 4, s);
+    for (int b = 0; b < 2; ++b) {
+      if (kbuf[b] && kbuf[b] != h->keys) dfree(h, kbuf[b], M * kw * 8, s);
+      if (vbuf[b] && vbuf[b] != h->vals) dfree(h, vbuf[b], M * 4, s);
+    }
+    dfree(h, table, entries * 4, s);
+    dfree(h, table_scan, entries * 4, s);
+    dfree(h, block_sums, std::max<size_t>(nblocks, 1) * 4, s);
+    dfree(h, counts, sum_dims * 4, s);
+    dfree(h, hot_scratch, 64 * 4, s);
+    dfree(h, counts_ptrs_dev, kMaxModes * sizeof(void *), s);
+    dfree(h, hot_list, ALTO_MAX_HOT * 8, s);
+  };
+  auto bail2 = [&](alto_status code) {
+    cleanup();
+    cudaStreamSynchronize(s);
+    alto_free(h);
+    return code;
+  };
+
+  if (M > 0) {
+    if (!is_device_ptr(coords)) {
+      if ((st = alloc_n(h, &coords_d, (size_t)N * M, s, "coords copy")) != ALTO_OK) return bail2(st);
+      own_coords = true;
+      if (cudaMemcpyAsync(coords_d, coords, (size_t)N * M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return bail2(fail(ALTO_ERR_CUDA, "copying coords"));
+    }
+    if (!is_device_ptr(vals)) {
+      if ((st = alloc_n(h, &vals_d, M, s, "vals copy")) != ALTO_OK) return bail2(st);
+      own_vals = true;
+      if (cudaMemcpyAsync(vals_d, vals, M * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return bail2(fail(ALTO_ERR_CUDA, "copying vals"));
+    }
+  }
+  for (int b = 0; b < 2; ++b) {
+    if ((st = alloc_n(h, &kbuf[b], (size_t)M * kw, s, "keys")) != ALTO_OK) return bail2(st);
+    if ((st = alloc_n(h, &vbuf[b], M, s, "values")) != ALTO_OK) return bail2(st);
+  }
+  if ((st = alloc_n(h, &table, entries, s, "sort table")) != ALTO_OK) return bail2(st);
+  if ((st = alloc_n(h, &table_scan, entries, s, "sort offsets")) != ALTO_OK) return bail2(st);
+  if ((st = alloc_n(h, &block_sums, std::max<size_t>(nblocks, 1), s, "scan sums")) != ALTO_OK)
+    return bail2(st);
+
+  cudaError_t e = launch_linearize(h->dp, coords_d, vals_d, M, h->dims_dev, kbuf[0], h->norm_sq_dev,
+                                   h->status_dev, h->num_sms, s);
+  if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "linearize: %s", cudaGetErrorString(e)));
+  int fb = 0;
+  e = launch_radix_sort(kw, h->nbits, M, kbuf, vbuf, vals_d, table, table_scan, block_sums, &fb, s);
+  if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e)));
+  h->keys = kbuf[fb];
+  h->vals = vbuf[fb];
+
+  if ((st = run_partition(h, default_parts(M, h->num_sms), s)) != ALTO_OK) return bail2(st);
+
+  // hot rows per mode
+  if (M > 0) {
+    if ((st = alloc_n(h, &counts, sum_dims, s, "row counts")) != ALTO_OK) return bail2(st);
+    if ((st = alloc_n(h, &hot_scratch, 64, s, "hot scratch")) != ALTO_OK) return bail2(st);
+    if ((st = alloc_n(h, &counts_ptrs_dev, kMaxModes, s, "count pointers")) != ALTO_OK) return bail2(st);
+    if ((st = alloc_n(h, &hot_list, ALTO_MAX_HOT, s, "hot list")) != ALTO_OK) return bail2(st);
+    uint32_t *cp[kMaxModes] = {};
+    uint64_t off = 0;
+    for (int n = 0; n < N; ++n) {
+      cp[n] = counts + off;
+      off += dims[n];
+    }
+    if (cudaMemsetAsync(counts, 0, sum_dims * 4, s) != cudaSuccess ||
+        cudaMemcpyAsync(counts_ptrs_dev, cp, sizeof(cp), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return bail2(fail(ALTO_ERR_CUDA, "hot-row setup"));
+    e = launch_hot_rows(h->dp, h->keys, M, h->dims, h->L, counts_ptrs_dev, cp, hot_scratch, hot_list,
+                        h->hot_rows, h->nhot_dev, h->num_sms, s);
+    if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "hot rows: %s", cudaGetErrorString(e)));
+  }
+  uint32_t status = 0;
+  if (cudaMemcpyAsync(&status, h->status_dev, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&h->norm_sq, h->norm_sq_dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(h->nhot, h->nhot_dev, kMaxModes * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return bail2(fail(ALTO_ERR_CUDA, "reading back encode results"));
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "encode: %s", cudaGetErrorString(e)));
+  if (status & kStatusCoordRange) return bail2(fail(ALTO_ERR_COORD_RANGE, "coordinate >= dims"));
+  for (int n = 0; n < N; ++n) {
+    h->hot_host[n].resize(h->nhot[n]);
+    if (h->nhot[n] &&
+        cudaMemcpy(h->hot_host[n].data(), h->hot_rows[n], h->nhot[n] * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail2(fail(ALTO_ERR_CUDA, "reading hot rows"));
+  }
+  cleanup();
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    alto_free(h);
+    return fail(ALTO_ERR_CUDA, "encode cleanup: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return ALTO_OK;
+}
+
+void alto_free(alto_handle_t h) {
+  if (!h) return;
+  cudaStream_t s = h->stream;
+  for (auto &pe : h->prof_pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto e : h->prof_pool) cudaEventDestroy(e);
+  for (int n = 0; n < kMaxModes; ++n) {
+    free_pull(h, n, s);
+    free_hot(h, n, s);
+    if (h->hot_rows[n]) dfree(h, h->hot_rows[n], ALTO_MAX_HOT * 4, s);
+  }
+  dfree(h, h->partials.p, h->partials.bytes, s);
+  dfree(h, h->keys, h->M * h->kw * 8, s);
+  dfree(h, h->vals, h->M * 4, s);
+  dfree(h, h->dims_dev, kMaxModes * 8, s);
+  dfree(h, h->intervals, h->L * h->N * 2 * 4, s);
+  dfree(h, h->max_len_dev, kMaxModes * 4, s);
+  dfree(h, h->status_dev, 4 * 4, s);
+  dfree(h, h->norm_sq_dev, 8, s);
+  dfree(h, h->nhot_dev, kMaxModes * 4, s);
+  delete h;
+}
+
+alto_status alto_profile_enable(alto_handle_t h, int on) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  h->prof_on = on != 0;
+  return ALTO_OK;
+}
+
+alto_status alto_profile_read(alto_handle_t h, alto_profile *out, int reset) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  for (auto &pe : h->prof_pending) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventSynchronize(pe.b));
+    CUDA_TRY(cudaEventElapsedTime(&ms, pe.a, pe.b));
+    h->prof_ms[pe.kind] += ms;
+    h->prof_n[pe.kind] += 1;
+    h->prof_pool.push_back(pe.a);
+    h->prof_pool.push_back(pe.b);
+  }
+  h->prof_pending.clear();
+  if (out)
+    for (int k = 0; k < ALTO_PROF_KINDS; ++k) {
+      out->launches[k] = h->prof_n[k];
+      out->ms[k] = h->prof_ms[k];
+    }
+  if (reset)
+    for (int k = 0; k < ALTO_PROF_KINDS; ++k) {
+      h->prof_n[k] = 0;
+      h->prof_ms[k] = 0.0;
+    }
+  return ALTO_OK;
+}
+
+uint64_t alto_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+alto_status alto_query(alto_handle_t h, alto_info *info) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (!info) return fail(ALTO_ERR_INVALID_ARG, "info is NULL");
+  uint32_t status = 0;
+  CUDA_TRY(cudaMemcpyAsync(&status, h->status_dev, 4, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  memset(info, 0, sizeof(*info));
+  info->nmodes = h->N;
+  info->nbits = h->nbits;
+  info->key_words = h->kw;
+  info->status = (status & kStatusCoordRange)  ? ALTO_ERR_COORD_RANGE
+                 : (status & kStatusNotSpd)    ? ALTO_ERR_NOT_SPD
+                 : (status & kStatusTimeout)   ? ALTO_ERR_TIMEOUT
+                                               : ALTO_OK;
+  info->nnz = h->M;
+  info->nparts = h->L;
+  for (int n = 0; n < h->N; ++n) {
+    info->dims[n] = h->dims[n];
+    info->bits[n] = h->bits[n];
+    info->mask_lo[n] = h->mask_lo[n];
+    info->mask_hi[n] = h->mask_hi[n];
+    info->max_interval[n] = h->max_interval[n];
+    info->nhot[n] = h->nhot[n];
+  }
+  info->norm_sq = h->norm_sq;
+  info->device_bytes = h->bytes_held;
+  return ALTO_OK;
+}
+
+alto_status alto_set_partitions(alto_handle_t h, uint64_t nparts, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (nparts < 1 || nparts > 0xFFFFFFFFull) return fail(ALTO_ERR_INVALID_ARG, "nparts out of range");
+  h->stream = (cudaStream_t)stream;
+  return run_partition(h, nparts, h->stream);
+}
+
+alto_status alto_copy_partition(alto_handle_t h, uint64_t *starts, uint32_t *intervals) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (starts)
+    for (uint64_t l = 0; l <= h->L; ++l) starts[l] = (l * h->M) / h->L;
+  if (intervals) {
+    if ((st = ensure_intervals_host(h, h->stream)) != ALTO_OK) return st;
+    memcpy(intervals, h->intervals_host.data(), h->intervals_host.size() * 4);
+  }
+  return ALTO_OK;
+}
+
+alto_status alto_copy_encoded(alto_handle_t h, uint64_t *keys, float *vals, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  if (h->M == 0) return ALTO_OK;
+  if (keys)
+    CUDA_TRY(cudaMemcpyAsync(keys, h->keys, h->M * h->kw * 8, cudaMemcpyDeviceToDevice, s));
+  if (vals) CUDA_TRY(cudaMemcpyAsync(vals, h->vals, h->M * 4, cudaMemcpyDeviceToDevice, s));
+  return ALTO_OK;
+}
+
+alto_status alto_decode(alto_handle_t h, uint32_t *coords, float *vals, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (!coords && h->M) return fail(ALTO_ERR_INVALID_ARG, "coords is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  CUDA_TRY(launch_decode(h->dp, h->keys, h->M, coords, h->num_sms, s));
+  if (vals && h->M) CUDA_TRY(cudaMemcpyAsync(vals, h->vals, h->M * 4, cudaMemcpyDeviceToDevice, s));
+  return ALTO_OK;
+}
+
+alto_status alto_copy_hot_rows(alto_handle_t h, int mode, uint32_t *rows, uint32_t cap,
+                               uint32_t *count) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < 0 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "mode %d out of range", mode);
+  if (count) *count = h->nhot[mode];
+  if (rows) {
+    const uint32_t k = std::min<uint32_t>(cap, h->nhot[mode]);
+    memcpy(rows, h->hot_host[mode].data(), k * 4);
+  }
+  return ALTO_OK;
+}
+
+alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *plan) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < 0 || mode >= h->N || !plan) return fail(ALTO_ERR_INVALID_ARG, "bad mode or plan");
+  if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_PULL)
+    return fail(ALTO_ERR_INVALID_ARG, "unknown variant %d", plan->variant);
+  if (plan->cols_per_lane != 0 && plan->cols_per_lane != 4 && plan->cols_per_lane != 8)
+    return fail(ALTO_ERR_INVALID_ARG, "cols_per_lane must be 0, 4 or 8");
+  h->plan[mode] = *plan;
+  return ALTO_OK;
+}
+
+alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan *plan) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < 0 || mode >= h->N || !plan) return fail(ALTO_ERR_INVALID_ARG, "bad mode or plan");
+  if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  return resolve_plan(h, mode, R, plan);
+}
+
+alto_status alto_mttkrp(alto_handle_t h, int mode, const void *const *factors, alto_dtype fdtype,
+                        int R, float *out, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < 0 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "mode %d out of range", mode);
+  if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  if (fdtype != ALTO_F32 && fdtype != ALTO_BF16) return fail(ALTO_ERR_INVALID_ARG, "bad dtype");
+  if (!factors || !out) return fail(ALTO_ERR_INVALID_ARG, "factors/out NULL");
+  if (!aligned16(out)) return fail(ALTO_ERR_INVALID_ARG, "out not 16-byte aligned");
+  for (int m = 0; m < h->N; ++m) {
+    if (m == mode) continue;
+    if (!factors[m]) return fail(ALTO_ERR_INVALID_ARG, "factors[%d] is NULL", m);
+    if (!aligned16(factors[m])) return fail(ALTO_ERR_INVALID_ARG, "factors[%d] not 16-byte aligned", m);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  return mttkrp_impl(h, mode, factors, fdtype == ALTO_BF16, R, out, s);
+}
+
+alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, double *lambda,
+                      double *fits, double tol, int *iters_done, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  if (iters < 1) return fail(ALTO_ERR_INVALID_ARG, "iters must be >= 1");
+  if (h->M == 0) return fail(ALTO_ERR_INVALID_ARG, "CP-ALS needs nnz > 0");
+  if (!factors || !lambda) return fail(ALTO_ERR_INVALID_ARG, "factors/lambda NULL");
+  if (!(tol >= 0.0)) return fail(ALTO_ERR_INVALID_ARG, "tol must be >= 0");
+  const int N = h->N;
+  int ndev = 0;
+  for (int m = 0; m < N; ++m) {
+    if (!factors[m]) return fail(ALTO_ERR_INVALID_ARG, "factors[%d] is NULL", m);
+    if (!aligned16(factors[m])) return fail(ALTO_ERR_INVALID_ARG, "factors[%d] not 16-byte aligned", m);
+    ndev += is_device_ptr(factors[m]) ? 1 : 0;
+  }
+  if (ndev != 0 && ndev != N) return fail(ALTO_ERR_INVALID_ARG, "factors mix host and device memory");
+  const bool host_factors = ndev == 0;
+  const bool host_lambda = !is_device_ptr(lambda);
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+
+  uint64_t maxI = 0, sumI = 0;
+  for (int m = 0; m < N; ++m) {
+    maxI = std::max(maxI, h->dims[m]);
+    sumI += h->dims[m];
+  }
+  const size_t RR = (size_t)R * R;
+  // one workspace: M | G[N] | MtM | W | fits | lambda | ints | device factors
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_MtM = take(RR * 8),
+               o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
+               o_int = take(16), o_fac = take(host_factors ? sumI * R * 4 : 0);
+  char *ws = static_cast<char *>(dalloc(h, off, s));
+  if (!ws) return fail(ALTO_ERR_OOM, "CP-ALS workspace of %zu bytes", off);
+  float *Mbuf = reinterpret_cast<float *>(ws + o_M);
+  double *G = reinterpret_cast<double *>(ws + o_G);
+  double *MtM = reinterpret_cast<double *>(ws + o_MtM);
+  float *W = reinterpret_cast<float *>(ws + o_W);
+  double *fits_d = reinterpret_cast<double *>(ws + o_fits);
+  double *lam_d = host_lambda ? reinterpret_cast<double *>(ws + o_lam) : lambda;
+  int *done_at = reinterpret_cast<int *>(ws + o_int);
+  int *iters_done_d = done_at + 1;
+  float *A[kMaxModes];
+  {
+    size_t fo = o_fac;
+    for (int m = 0; m < N; ++m) {
+      if (host_factors) {
+        A[m] = reinterpret_cast<float *>(ws + fo);
+        fo += h->dims[m] * R * 4;
+      } else {
+        A[m] = factors[m];
+      }
+    }
+  }
+  auto finish = [&](alto_status code) {
+    dfree(h, ws, off, s);
+    return code;
+  };
+#define CP_TRY(expr)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return finish(fail(ALTO_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
+  } while (0)
+  if (host_factors)
+    for (int m = 0; m < N; ++m)
+      CP_TRY(cudaMemcpyAsync(A[m], factors[m], h->dims[m] * R * 4, cudaMemcpyHostToDevice, s));
+  CP_TRY(cudaMemsetAsync(done_at, 0x7F, sizeof(int), s));
+  CP_TRY(cudaMemsetAsync(iters_done_d, 0, sizeof(int), s));
+  CP_TRY(cudaMemsetAsync(G, 0, N * RR * 8, s));
+  CP_TRY(cudaMemsetAsync(fits_d, 0, (size_t)iters * 8, s));
+  for (int m = 0; m < N; ++m) {
+    ProfScope ps(h, ALTO_PROF_GRAM, s);
+    CP_TRY(launch_gram(A[m], h->dims[m], R, G + m * RR, nullptr, 0, h->num_sms, s));
+  }
+  const void *fptr[kMaxModes];
+  for (int m = 0; m < N; ++m) fptr[m] = A[m];
+  for (int it = 0; it < iters; ++it) {
+    for (int n = 0; n < N; ++n) {
+      st = mttkrp_impl(h, n, fptr, false, R, Mbuf, s);
+      if (st != ALTO_OK) return finish(st);
+      CP_TRY(cudaMemsetAsync(MtM, 0, RR * 8, s));
+      {
+        ProfScope ps(h, ALTO_PROF_GRAM, s);
+        CP_TRY(launch_gram(Mbuf, h->dims[n], R, MtM, done_at, it, h->num_sms, s));
+      }
+      SolveArgs sa{};
+      sa.G = G;
+      sa.G_out = G + n * RR;
+      sa.MtM = MtM;
+      sa.W = W;
+      sa.lambda = lam_d;
+      sa.fits = fits_d;
+      sa.norm_sq = h->norm_sq_dev;
+      sa.done_at = done_at;
+      sa.iters_done = iters_done_d;
+      sa.status = h->status_dev;
+      sa.N = N;
+      sa.n = n;
+      sa.R = R;
+      sa.it = it;
+      sa.last_mode = n == N - 1;
+      sa.tol = tol;
+      {
+        ProfScope ps(h, ALTO_PROF_SOLVE, s);
+        CP_TRY(launch_solve(sa, s));
+      }
+      {
+        ProfScope ps(h, ALTO_PROF_RMUL, s);
+        CP_TRY(launch_rmul(Mbuf, W, A[n], h->dims[n], R, done_at, it, h->num_sms, s));
+      }
+    }
+    if (tol > 0.0 && it + 1 < iters) {
+      int d = INT_MAX;
+      CP_TRY(cudaMemcpyAsync(&d, done_at, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CP_TRY(cudaStreamSynchronize(s));
+      if (d <= it + 1) break;
+    }
+  }
+  if (host_lambda) CP_TRY(cudaMemcpyAsync(lambda, lam_d, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
+  if (host_factors)
+    for (int m = 0; m < N; ++m)
+      CP_TRY(cudaMemcpyAsync(factors[m], A[m], h->dims[m] * R * 4, cudaMemcpyDeviceToHost, s));
+  int nd = 0;
+  uint32_t status = 0;
+  if (fits) CP_TRY(cudaMemcpyAsync(fits, fits_d, (size_t)iters * 8, cudaMemcpyDeviceToHost, s));
+  CP_TRY(cudaMemcpyAsync(&nd, iters_done_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CP_TRY(cudaMemcpyAsync(&status, h->status_dev, 4, cudaMemcpyDeviceToHost, s));
+  CP_TRY(cudaStreamSynchronize(s));
+  if (iters_done) *iters_done = nd;
+#undef CP_TRY
+  if (status & kStatusNotSpd) {
+    const uint32_t zero = 0;
+    cudaMemcpyAsync(h->status_dev, &zero, 4, cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    return finish(fail(ALTO_ERR_NOT_SPD, "V of Alg. 1 is not positive definite"));
+  }
+  return finish(ALTO_OK);
+}
+
+}  // extern "C"

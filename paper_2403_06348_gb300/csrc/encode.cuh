@@ -1,0 +1,31 @@
+// Host-side launchers of the encode kernels (encode.cu).
+#pragma once
+
+#include "alto_internal.cuh"
+
+namespace alto {
+
+cudaError_t launch_linearize(const DecodePlan &dp, const uint32_t *coords, const float *vals,
+                             uint64_t nnz, const uint64_t *dims_dev, uint64_t *keys,
+                             double *norm_sq, uint32_t *status, int num_sms, cudaStream_t s);
+
+size_t sort_table_entries(uint64_t nnz);
+size_t sort_scan_blocks(uint64_t nnz);
+
+cudaError_t launch_radix_sort(int kw, int nbits, uint64_t nnz, uint64_t *keys[2], float *vals[2],
+                              const float *vals_in, uint32_t *table, uint32_t *table_scan,
+                              uint32_t *block_sums, int *final_buf, cudaStream_t s);
+
+cudaError_t launch_partition(const DecodePlan &dp, const uint64_t *keys, uint64_t nnz, uint64_t L,
+                             uint32_t *intervals, uint32_t *max_len, int num_sms, cudaStream_t s);
+
+cudaError_t launch_hot_rows(const DecodePlan &dp, const uint64_t *keys, uint64_t nnz,
+                            const uint64_t *dims, uint64_t L, uint32_t *const *counts_dev_ptrs,
+                            uint32_t *const *counts_host_ptrs, uint32_t *scratch, uint64_t *list,
+                            uint32_t *const *hot_rows, uint32_t *nhot, int num_sms,
+                            cudaStream_t s);
+
+cudaError_t launch_decode(const DecodePlan &dp, const uint64_t *keys, uint64_t nnz, uint32_t *coords,
+                          int num_sms, cudaStream_t s);
+
+}  // namespace alto

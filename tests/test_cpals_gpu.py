@@ -1,0 +1,88 @@
+"""GPU CP-ALS (Alg. 1) through the C ABI against the fp64 oracle.
+
+MTTKRP parity is the hard gate; CP-ALS is a trajectory check: the fit after
+every iteration within 1e-4 of the oracle's, columns normalised, exact low-rank
+tensors recovered.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import alto_ref as ar
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    gu.ensure_built()
+
+
+def _oracle_cpals(coords, vals, dims, init, iters, tol=0.0):
+    return ar.cp_als(coords, vals, dims, init, iters, tol=tol)
+
+
+@pytest.mark.parametrize("R", [8, 16])
+def test_fit_trajectory_matches_oracle(R):
+    spec = synth.scaled(synth.CONFIGS[0], 20_000, dims=(200, 160, 120))
+    coords, vals = synth.generate(spec)
+    init = gu.rand_factors(spec.dims, R, 3)
+    ref = _oracle_cpals(coords, vals, spec.dims, init, iters=6)
+    t = gu.encode(coords, vals, spec.dims)
+    A = gu.gpu_factors(init)
+    lam, fits = t.cpals(R, 6, A)
+    assert len(fits) == 6
+    np.testing.assert_allclose(fits, ref.fits, atol=1e-4)
+    for a in A:
+        np.testing.assert_allclose(a.norm(dim=0).cpu().numpy(), 1.0, rtol=1e-4)
+    np.testing.assert_allclose(lam, ref.lam, rtol=1e-2)
+
+
+def test_exact_low_rank_recovered():
+    """An exact rank-4 tensor decomposed at R = 4 reaches fit 1 (up to fp32)."""
+    rng = np.random.default_rng(1)
+    dims, R = (60, 50, 40), 4
+    F = [np.abs(rng.standard_normal((d, R))) * (rng.random((d, 1)) < 0.6) for d in dims]
+    X = ar.reconstruct_dense(np.ones(R), F)
+    nz = np.nonzero(X)
+    coords = np.stack(nz).astype(np.uint32)
+    vals = X[nz].astype(np.float32)
+    t = gu.encode(coords, vals, dims)
+    A = gu.gpu_factors([np.random.default_rng(2).random((d, R)).astype(np.float32) for d in dims])
+    lam, fits = t.cpals(R, 150, A)
+    assert fits[-1] > 1 - 1e-4
+
+
+def test_tol_stops_early_and_host_factors_match_device():
+    spec = synth.scaled(synth.CONFIGS[0], 10_000, dims=(100, 90, 80))
+    coords, vals = synth.generate(spec)
+    init = gu.rand_factors(spec.dims, 8, 5)
+    t = gu.encode(coords, vals, spec.dims)
+    Ad = gu.gpu_factors(init)
+    lam_d, fits_d = t.cpals(8, 50, Ad, tol=1e-3)
+    assert 1 < len(fits_d) < 50
+    assert abs(fits_d[-1] - fits_d[-2]) < 1e-3
+    Ah = [a.copy() for a in init]
+    lam_h, fits_h = t.cpals(8, 50, Ah, tol=1e-3)
+    assert len(fits_h) == len(fits_d)
+    np.testing.assert_allclose(fits_h, fits_d, atol=1e-5)
+    for a, b in zip(Ah, Ad):
+        np.testing.assert_allclose(a, b.cpu().numpy(), atol=1e-4)
+
+
+def test_singular_gram_reports_not_spd():
+    import paper_2403_06348_gb300 as alto
+    dims = (30, 20, 10)
+    coords, vals = gu.rand_tensor(dims, 2000, 4)
+    t = gu.encode(coords, vals, dims)
+    init = gu.rand_factors(dims, 4, 6)
+    for a in init:
+        a[:, 1] = 0.0          # a zero column in every factor: V has a zero pivot
+    A = gu.gpu_factors(init)
+    with pytest.raises(alto.AltoError) as e:
+        t.cpals(4, 3, A)
+    assert e.value.status == -6
+    # the handle stays usable
+    A2 = gu.gpu_factors(gu.rand_factors(dims, 4, 7))
+    t.cpals(4, 2, A2)
