@@ -25,6 +25,8 @@ Readings of the paper that this file fixes (each also listed in the design doc):
   every iteration, a zero column gets lambda 0 and stays unscaled; the fit is
   1 - ||X - X_hat|| / ||X|| evaluated with the usual expansion
   ||X||^2 + lambda^T (*_m G_m) lambda - 2 <X, X_hat>.
+* Duplicate coordinates are separate COO entries that add up into one cell of
+  X: MTTKRP sums them term by term, and ||X||^2 squares the summed cells.
 """
 from __future__ import annotations
 
@@ -307,6 +309,18 @@ def _solve_spd_or_pinv(V: np.ndarray, M: np.ndarray) -> np.ndarray:
         return M @ np.linalg.pinv(V)
 
 
+def tensor_norm_sq(coords: np.ndarray, vals: np.ndarray) -> float:
+    """||X||^2 of the tensor the COO entries describe: entries with the same
+    coordinates add up into one cell (Section II-C, COO), then the cells are
+    squared and summed."""
+    if coords.shape[1] == 0:
+        return 0.0
+    _, inv = np.unique(np.asarray(coords).T, axis=0, return_inverse=True)
+    cells = np.zeros(int(inv.max()) + 1)
+    np.add.at(cells, inv.ravel(), np.asarray(vals, dtype=np.float64))
+    return float(np.sum(cells * cells))
+
+
 def cp_fit(normX2: float, lam: np.ndarray, factors: Sequence[np.ndarray],
            M_last: np.ndarray) -> float:
     """1 - ||X - X_hat|| / ||X|| from lambda, the Grams and the last MTTKRP."""
@@ -361,7 +375,7 @@ def cp_als(coords: np.ndarray, vals: np.ndarray, dims: Sequence[int],
     A = [np.asarray(f, dtype=np.float64).copy() for f in init]
     R = A[0].shape[1]
     lam = np.ones(R)
-    normX2 = float(np.sum(np.asarray(vals, dtype=np.float64) ** 2))
+    normX2 = tensor_norm_sq(coords, vals)
     fits: List[float] = []
     prev: Optional[float] = None
     for _ in range(iters):

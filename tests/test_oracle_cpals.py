@@ -54,6 +54,24 @@ def test_fit_matches_dense_residual():
     assert abs(direct - res.fits[-1]) < 1e-10
 
 
+def test_norm_and_fit_with_duplicate_coordinates():
+    """Duplicates add up into one cell: ||X||^2 and the fit follow the dense
+    tensor built with np.add.at."""
+    rng = np.random.default_rng(3)
+    dims, R = (5, 4, 3), 2
+    M = 200
+    coords = np.stack([rng.integers(0, d, M) for d in dims]).astype(np.uint32)
+    vals = rng.random(M).astype(np.float32)
+    X = ar.to_dense(coords, vals, dims)
+    assert abs(ar.tensor_norm_sq(coords, vals) - np.sum(X * X)) < 1e-9 * np.sum(X * X)
+    assert ar.tensor_norm_sq(coords, vals) > 1.5 * np.sum(vals.astype(np.float64) ** 2)
+    init = [rng.random((d, R)) for d in dims]
+    res = ar.cp_als(coords, vals, dims, init, iters=4)
+    Xh = ar.reconstruct_dense(res.lam, res.factors)
+    direct = 1 - np.linalg.norm(X - Xh) / np.linalg.norm(X)
+    assert abs(direct - res.fits[-1]) < 1e-10
+
+
 @pytest.mark.parametrize("R", [1, 2])
 def test_exact_low_rank_recovered(R):
     dims = (8, 7, 6)
