@@ -102,8 +102,9 @@ typedef struct alto_info {
 /* Per-mode MTTKRP plan (what the autotuner sets). */
 typedef struct alto_mode_plan {
   int variant;        /* alto_variant                                             */
-  int cols_per_lane;  /* 4 or 8 factor columns per thread: R/cols_per_lane threads
-                         work on one nonzero ("threads per nonzero")              */
+  int cols_per_lane;  /* 4, 8 or 16 factor columns per thread: R/cols_per_lane
+                         threads work on one nonzero ("threads per nonzero");
+                         0 = library default                                    */
   int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit             */
 } alto_mode_plan;
 
@@ -236,9 +237,10 @@ typedef enum alto_prof_kind {
   ALTO_PROF_MTTKRP = 0,       /* the segment kernel of Alg. 3/4             */
   ALTO_PROF_PULL_REDUCE = 1,  /* the pull-based reduction of Alg. 4         */
   ALTO_PROF_ZERO = 2,         /* zeroing of the output (ATOMIC variant)      */
-  ALTO_PROF_GRAM = 3,         /* A^T A of a factor or of M                  */
+  ALTO_PROF_GRAM = 3,         /* A^T A of the initial factors                */
   ALTO_PROF_SOLVE = 4,        /* fp64 Hadamard / Cholesky / lambda / fit    */
-  ALTO_PROF_RMUL = 5,         /* A^(n) = M V^-1 diag(1/lambda)              */
+  ALTO_PROF_RMUL = 5,         /* A^(n) = M V^-1 with its Gram (one pass) and
+                                 the final column normalisation             */
   ALTO_PROF_KINDS = 6
 } alto_prof_kind;
 

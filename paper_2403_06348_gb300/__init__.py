@@ -294,7 +294,8 @@ class AltoTensor:
         if dtype is not None:
             code = dtype
         if out is None:
-            out = torch.empty((self.dims[mode], R), dtype=torch.float32, device="cuda")
+            rows = self.dims[mode] if 0 <= mode < self.nmodes else 1  # the C call rejects bad modes
+            out = torch.empty((rows, R), dtype=torch.float32, device="cuda")
         alto_mttkrp(self, mode, factors, R, out, code, stream)
         return out
 

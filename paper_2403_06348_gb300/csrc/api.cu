@@ -379,8 +379,8 @@ alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) 
 
 bool rank_ok(int R) { return R == 4 || R == 8 || R == 16 || R == 32 || R == 64; }
 
-// Shared memory budget per CTA for the staged tables: two CTAs per SM.
-size_t stage_budget() { return std::min<size_t>(mttkrp_smem_limit(), 110 * 1024); }
+// Shared memory budget of the staged tables: one persistent CTA per SM.
+size_t stage_budget() { return mttkrp_smem_limit() - 1024; }
 
 int hot_slots_that_fit(int R, int want) {
   const size_t budget = stage_budget();
@@ -396,8 +396,9 @@ int hot_slots_that_fit(int R, int want) {
 
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   alto_mode_plan p = h->plan[mode];
-  if (p.cols_per_lane != 4 && p.cols_per_lane != 8) p.cols_per_lane = (R % 8 == 0) ? 8 : 4;
-  if (R % p.cols_per_lane) p.cols_per_lane = 4;
+  if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16)
+    p.cols_per_lane = (R % 8 == 0) ? 8 : 4;
+  while (R % p.cols_per_lane) p.cols_per_lane /= 2;
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
   const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
@@ -431,16 +432,30 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
   if (st != ALTO_OK) return st;
   const uint64_t I = h->dims[mode];
   MttkrpArgs a{};
-  a.dp = h->dp;
+  // coordinate 0 of the kernel's decode is the output mode
+  int order[kMaxModes];
+  order[0] = mode;
+  for (int m = 0, j = 1; m < h->N; ++m)
+    if (m != mode) order[j++] = m;
+  a.dp.nmodes = h->N;
+  a.dp.kw = h->kw;
+  for (int j = 0; j < h->N; ++j) {
+    a.dp.nruns[j] = h->dp.nruns[order[j]];
+    memcpy(a.dp.runs[j], h->dp.runs[order[j]], sizeof(a.dp.runs[j]));
+    a.factors[j] = j ? factors[order[j]] : nullptr;
+  }
   a.keys = h->keys;
   a.vals = h->vals;
   a.nnz = h->M;
   a.L = h->L;
   a.intervals = h->intervals;
-  for (int m = 0; m < h->N; ++m) a.factors[m] = factors[m];
   a.out = out;
   a.mode = mode;
   a.R = R;
+  {
+    const uint64_t per_seg = std::max<uint64_t>(h->M / std::max<uint64_t>(h->L, 1), 1);
+    a.flush_every = (int)std::max<uint64_t>(1, 32768 / per_seg);
+  }
   if (h->M == 0) {
     CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
     return ALTO_OK;
@@ -621,14 +636,31 @@ alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_
   if ((st = alloc_n(h, &block_sums, std::max<size_t>(nblocks, 1), s, "scan sums")) != ALTO_OK)
     return bail2(st);
 
-  cudaError_t e = launch_linearize(h->dp, coords_d, vals_d, M, h->dims_dev, kbuf[0], h->norm_sq_dev,
-                                   h->status_dev, h->num_sms, s);
+  cudaError_t e = launch_linearize(h->dp, coords_d, M, h->dims_dev, kbuf[0], h->status_dev,
+                                   h->num_sms, s);
   if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "linearize: %s", cudaGetErrorString(e)));
   int fb = 0;
   e = launch_radix_sort(kw, h->nbits, M, kbuf, vbuf, vals_d, table, table_scan, block_sums, &fb, s);
   if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e)));
   h->keys = kbuf[fb];
   h->vals = vbuf[fb];
+  {
+    // ||X||^2 over cells (duplicates summed); scratch reuses the other key buffer
+    const uint64_t nc = norm_chunks(M);
+    char *scr = reinterpret_cast<char *>(kbuf[fb ^ 1]);
+    const size_t need = nc * (8 + 8 + 1);
+    char *tmp = nullptr;
+    if (need > (size_t)M * kw * 8) {
+      tmp = static_cast<char *>(dalloc(h, need, s));
+      if (!tmp) return bail2(fail(ALTO_ERR_OOM, "norm scratch"));
+      scr = tmp;
+    }
+    e = launch_norm(kw, h->keys, h->vals, M, reinterpret_cast<double *>(scr),
+                    reinterpret_cast<double *>(scr + nc * 8), reinterpret_cast<uint8_t *>(scr + nc * 16),
+                    h->norm_sq_dev, h->num_sms, s);
+    if (tmp) dfree(h, tmp, need, s);
+    if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "norm: %s", cudaGetErrorString(e)));
+  }
 
   if ((st = run_partition(h, default_parts(M, h->num_sms), s)) != ALTO_OK) return bail2(st);
 
@@ -827,8 +859,9 @@ alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *
   if (mode < 0 || mode >= h->N || !plan) return fail(ALTO_ERR_INVALID_ARG, "bad mode or plan");
   if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_PULL)
     return fail(ALTO_ERR_INVALID_ARG, "unknown variant %d", plan->variant);
-  if (plan->cols_per_lane != 0 && plan->cols_per_lane != 4 && plan->cols_per_lane != 8)
-    return fail(ALTO_ERR_INVALID_ARG, "cols_per_lane must be 0, 4 or 8");
+  if (plan->cols_per_lane != 0 && plan->cols_per_lane != 4 && plan->cols_per_lane != 8 &&
+      plan->cols_per_lane != 16)
+    return fail(ALTO_ERR_INVALID_ARG, "cols_per_lane must be 0, 4, 8 or 16");
   h->plan[mode] = *plan;
   return ALTO_OK;
 }
@@ -888,21 +921,25 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
     sumI += h->dims[m];
   }
   const size_t RR = (size_t)R * R;
-  // one workspace: M | G[N] | MtM | W | fits | lambda | ints | device factors
+  // one workspace: M | G[N] | s[N] | Sn | BtB | dot | W | fits | lambda | ints | device factors
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
     off += (bytes + 255) & ~(size_t)255;
     return o;
   };
-  const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_MtM = take(RR * 8),
+  const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_s = take((size_t)N * R * 8),
+               o_Sn = take((size_t)R * 8), o_BtB = take(RR * 8), o_dot = take((size_t)R * 8),
                o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
                o_int = take(16), o_fac = take(host_factors ? sumI * R * 4 : 0);
   char *ws = static_cast<char *>(dalloc(h, off, s));
   if (!ws) return fail(ALTO_ERR_OOM, "CP-ALS workspace of %zu bytes", off);
   float *Mbuf = reinterpret_cast<float *>(ws + o_M);
   double *G = reinterpret_cast<double *>(ws + o_G);
-  double *MtM = reinterpret_cast<double *>(ws + o_MtM);
+  double *scl = reinterpret_cast<double *>(ws + o_s);
+  double *Sn = reinterpret_cast<double *>(ws + o_Sn);
+  double *BtB = reinterpret_cast<double *>(ws + o_BtB);
+  double *dot = reinterpret_cast<double *>(ws + o_dot);
   float *W = reinterpret_cast<float *>(ws + o_W);
   double *fits_d = reinterpret_cast<double *>(ws + o_fits);
   double *lam_d = host_lambda ? reinterpret_cast<double *>(ws + o_lam) : lambda;
@@ -932,49 +969,56 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
   if (host_factors)
     for (int m = 0; m < N; ++m)
       CP_TRY(cudaMemcpyAsync(A[m], factors[m], h->dims[m] * R * 4, cudaMemcpyHostToDevice, s));
+  {
+    std::vector<double> ones((size_t)N * R, 1.0);
+    CP_TRY(cudaMemcpyAsync(scl, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, s));
+  }
   CP_TRY(cudaMemsetAsync(done_at, 0x7F, sizeof(int), s));
   CP_TRY(cudaMemsetAsync(iters_done_d, 0, sizeof(int), s));
   CP_TRY(cudaMemsetAsync(G, 0, N * RR * 8, s));
   CP_TRY(cudaMemsetAsync(fits_d, 0, (size_t)iters * 8, s));
   for (int m = 0; m < N; ++m) {
     ProfScope ps(h, ALTO_PROF_GRAM, s);
-    CP_TRY(launch_gram(A[m], h->dims[m], R, G + m * RR, nullptr, 0, h->num_sms, s));
+    CP_TRY(launch_gram(A[m], h->dims[m], R, G + m * RR, h->num_sms, s));
   }
   const void *fptr[kMaxModes];
   for (int m = 0; m < N; ++m) fptr[m] = A[m];
+  CpArgs ca{};
+  ca.G = G;
+  ca.s = scl;
+  ca.Sn = Sn;
+  ca.BtB = BtB;
+  ca.dot = dot;
+  ca.W = W;
+  ca.lambda = lam_d;
+  ca.fits = fits_d;
+  ca.norm_sq = h->norm_sq_dev;
+  ca.done_at = done_at;
+  ca.iters_done = iters_done_d;
+  ca.status = h->status_dev;
+  ca.N = N;
+  ca.R = R;
+  ca.tol = tol;
   for (int it = 0; it < iters; ++it) {
     for (int n = 0; n < N; ++n) {
-      st = mttkrp_impl(h, n, fptr, false, R, Mbuf, s);
-      if (st != ALTO_OK) return finish(st);
-      CP_TRY(cudaMemsetAsync(MtM, 0, RR * 8, s));
-      {
-        ProfScope ps(h, ALTO_PROF_GRAM, s);
-        CP_TRY(launch_gram(Mbuf, h->dims[n], R, MtM, done_at, it, h->num_sms, s));
-      }
-      SolveArgs sa{};
-      sa.G = G;
-      sa.G_out = G + n * RR;
-      sa.MtM = MtM;
-      sa.W = W;
-      sa.lambda = lam_d;
-      sa.fits = fits_d;
-      sa.norm_sq = h->norm_sq_dev;
-      sa.done_at = done_at;
-      sa.iters_done = iters_done_d;
-      sa.status = h->status_dev;
-      sa.N = N;
-      sa.n = n;
-      sa.R = R;
-      sa.it = it;
-      sa.last_mode = n == N - 1;
-      sa.tol = tol;
+      ca.n = n;
+      ca.it = it;
+      ca.last_mode = n == N - 1;
       {
         ProfScope ps(h, ALTO_PROF_SOLVE, s);
-        CP_TRY(launch_solve(sa, s));
+        CP_TRY(launch_prepare(ca, s));
       }
+      st = mttkrp_impl(h, n, fptr, false, R, Mbuf, s);
+      if (st != ALTO_OK) return finish(st);
+      CP_TRY(cudaMemsetAsync(BtB, 0, RR * 8, s));
+      CP_TRY(cudaMemsetAsync(dot, 0, (size_t)R * 8, s));
       {
         ProfScope ps(h, ALTO_PROF_RMUL, s);
-        CP_TRY(launch_rmul(Mbuf, W, A[n], h->dims[n], R, done_at, it, h->num_sms, s));
+        CP_TRY(launch_update(Mbuf, W, A[n], h->dims[n], R, BtB, dot, done_at, it, h->num_sms, s));
+      }
+      {
+        ProfScope ps(h, ALTO_PROF_SOLVE, s);
+        CP_TRY(launch_finish(ca, s));
       }
     }
     if (tol > 0.0 && it + 1 < iters) {
@@ -983,6 +1027,10 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
       CP_TRY(cudaStreamSynchronize(s));
       if (d <= it + 1) break;
     }
+  }
+  for (int m = 0; m < N; ++m) {
+    ProfScope ps(h, ALTO_PROF_RMUL, s);
+    CP_TRY(launch_scale(A[m], scl + (size_t)m * R, h->dims[m], R, h->num_sms, s));
   }
   if (host_lambda) CP_TRY(cudaMemcpyAsync(lambda, lam_d, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
   if (host_factors)

@@ -1,25 +1,29 @@
-// CP-ALS glue of Alg. 1 around the MTTKRP:
-//   gram_kernel   G = A^T A (fp32 products, fp32 partial sums over at most
-//                 1024 rows, fp64 combine)
-//   solve_kernel  one CTA, fp64: V = Hadamard of the other Grams, Cholesky
-//                 V = L L^T, V^-1, lambda_r = ||(M V^-1)(:,r)|| from
-//                 V^-1 (M^T M) V^-1, W = V^-1 diag(1/lambda), the new Gram
-//                 diag(1/lambda) V^-1 M^T M V^-1 diag(1/lambda), and after the
-//                 last mode the fit
-//   rmul_kernel   A^(n) = M W (fp32), i.e. the normalised M V^-1.
-// Every kernel returns at once when the run stopped early (done_at <= it).
+// CP-ALS glue of Alg. 1 around the MTTKRP.
+//
+// Per mode n (factors stored as B_m with A_m = B_m diag(s_m)):
+//   prepare_kernel  one CTA, fp64: V = Hadamard product of the other Grams,
+//                   Cholesky V = L L^T, V^-1, Sn = prod_{m != n} s_m and
+//                   W = diag(Sn) V^-1. MTTKRP over the stored B's gives
+//                   M_B = M diag(1/Sn), so M V^-1 = M_B W.
+//   (MTTKRP)
+//   update_kernel   B_n = M_B W in one pass over M_B, accumulating B_n^T B_n
+//                   and sum_i M_B(i,r) B_n(i,r) (fp32 partial sums over at most
+//                   1024 rows, fp64 combine).
+//   finish_kernel   one CTA, fp64: lambda_r = ||B_n(:,r)||, s_n = 1/lambda
+//                   (1 for a zero column), the new Gram diag(s_n) B^T B
+//                   diag(s_n), and after the last mode the fit.
+// gram_kernel gives the Grams of the initial factors; scale_kernel writes the
+// normalised A_m = B_m diag(s_m) once at the end of a run.
+// Every per-iteration kernel returns at once when the run has stopped
+// (done_at <= it).
 #include "cpals.cuh"
-
-#include <climits>
 
 namespace alto {
 
-constexpr int kGramRows = 32;  // rows staged per step
+constexpr int kGramRows = 32;
 
 __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, uint64_t I, int R,
-                                                   double *__restrict__ G,
-                                                   const int *__restrict__ done_at, int it) {
-  if (done_at && *done_at <= it) return;
+                                                   double *__restrict__ G) {
   __shared__ __align__(16) float tile[kGramRows * ALTO_MAX_RANK];
   __shared__ double red[ALTO_MAX_RANK * ALTO_MAX_RANK];
   const int B = R / 4, BB = B * B, RG = 256 / BB;
@@ -50,7 +54,7 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, 
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(xa[a], ya[b], acc[a][b]);
     }
-    if (++steps == 32) {  // at most 32*32 rows per fp32 partial
+    if (++steps == 32) {
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -74,111 +78,198 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, 
     if (red[i] != 0.0) atomicAdd(&G[i], red[i]);
 }
 
-// One CTA of 256 threads; all matrices R x R in shared memory (fp64).
-__global__ void __launch_bounds__(256) solve_kernel(const SolveArgs a) {
+// Cholesky of the R x R matrix in V (lower triangle overwritten by L).
+// Returns false if a pivot is not positive and finite.
+__device__ bool block_cholesky(double *V, int R, int *fail) {
+  const int tid = threadIdx.x;
+  for (int k = 0; k < R; ++k) {
+    if (tid == 0) {
+      const double d = V[k * R + k];
+      if (!(d > 0.0) || !isfinite(d)) *fail = 1;
+      V[k * R + k] = sqrt(d > 0.0 ? d : 1.0);
+    }
+    __syncthreads();
+    const double dk = V[k * R + k];
+    for (int i = k + 1 + tid; i < R; i += blockDim.x) V[i * R + k] /= dk;
+    __syncthreads();
+    const int m = R - k - 1;
+    for (int p = tid; p < m * m; p += blockDim.x) {
+      const int i = k + 1 + p / m, j = k + 1 + p % m;
+      if (j <= i) V[i * R + j] -= V[i * R + k] * V[j * R + k];
+    }
+    __syncthreads();
+  }
+  return *fail == 0;
+}
+
+__global__ void __launch_bounds__(256) prepare_kernel(const CpArgs a) {
   if (*a.done_at <= a.it) return;
   extern __shared__ __align__(16) double sd[];
   const int R = a.R, RR = R * R, tid = threadIdx.x;
-  double *V = sd;            // V, then its Cholesky factor L (lower)
-  double *Vi = V + RR;       // V^-1
-  double *T = Vi + RR;       // scratch
-  double *Gr = T + RR;       // V^-1 MtM V^-1
-  double *lam = Gr + RR;     // R
-  double *scl = lam + R;     // R: 1/lambda or 1
+  double *V = sd;       // V, then L
+  double *Vi = V + RR;  // V^-1
+  double *T = Vi + RR;  // forward-solve scratch
   __shared__ int fail;
   if (tid == 0) fail = 0;
-  // V = *_{m != n} G_m
-  for (int e = tid; e < RR; e += 256) {
+  for (int e = tid; e < RR; e += blockDim.x) {
     double v = 1.0;
     for (int m = 0; m < a.N; ++m)
       if (m != a.n) v *= a.G[(size_t)m * RR + e];
     V[e] = v;
   }
   __syncthreads();
-  // Cholesky, column by column (lower triangle of V overwritten by L)
-  for (int k = 0; k < R; ++k) {
-    if (tid == 0) {
-      const double d = V[k * R + k];
-      if (!(d > 0.0) || !isfinite(d)) fail = 1;
-      V[k * R + k] = sqrt(d > 0.0 ? d : 1.0);
-    }
-    __syncthreads();
-    const double dk = V[k * R + k];
-    for (int i = k + 1 + tid; i < R; i += 256) V[i * R + k] /= dk;
-    __syncthreads();
-    const int m = R - k - 1;
-    for (int p = tid; p < m * m; p += 256) {
-      const int i = k + 1 + p / m, j = k + 1 + p % m;
-      if (j <= i) V[i * R + j] -= V[i * R + k] * V[j * R + k];
-    }
-    __syncthreads();
-  }
-  if (fail) {
+  if (!block_cholesky(V, R, &fail)) {
     if (tid == 0) {
       atomicOr(a.status, kStatusNotSpd);
-      *a.done_at = a.it;  // stop: later kernels of this and further iterations skip
+      *a.done_at = a.it;
     }
     return;
   }
-  // V^-1 = L^-T L^-1, one column per thread
-  for (int j = tid; j < R; j += 256) {
-    for (int i = 0; i < R; ++i) {  // forward: L y = e_j
+  for (int j = tid; j < R; j += blockDim.x) {
+    for (int i = 0; i < R; ++i) {  // L y = e_j
       double s = (i == j) ? 1.0 : 0.0;
       for (int k = 0; k < i; ++k) s -= V[i * R + k] * T[k * R + j];
       T[i * R + j] = s / V[i * R + i];
     }
-    for (int i = R - 1; i >= 0; --i) {  // backward: L^T x = y
+    for (int i = R - 1; i >= 0; --i) {  // L^T x = y
       double s = T[i * R + j];
       for (int k = i + 1; k < R; ++k) s -= V[k * R + i] * Vi[k * R + j];
       Vi[i * R + j] = s / V[i * R + i];
     }
   }
-  __syncthreads();
-  // Gr = V^-1 MtM V^-1 (= (M V^-1)^T (M V^-1))
-  for (int e = tid; e < RR; e += 256) {
-    const int i = e / R, j = e % R;
-    double s = 0.0;
-    for (int k = 0; k < R; ++k) s += Vi[i * R + k] * a.MtM[k * R + j];
-    T[e] = s;
+  for (int r = tid; r < R; r += blockDim.x) {
+    double p = 1.0;
+    for (int m = 0; m < a.N; ++m)
+      if (m != a.n) p *= a.s[(size_t)m * R + r];
+    a.Sn[r] = p;
   }
   __syncthreads();
-  for (int e = tid; e < RR; e += 256) {
-    const int i = e / R, j = e % R;
-    double s = 0.0;
-    for (int k = 0; k < R; ++k) s += T[i * R + k] * Vi[k * R + j];
-    Gr[e] = s;
+  for (int e = tid; e < RR; e += blockDim.x) {
+    const int i = e / R;
+    a.W[e] = (float)(a.Sn[i] * Vi[e]);
+  }
+}
+
+// B = M W with B^T B and the column dot products of M and B, one pass.
+__global__ void __launch_bounds__(256) update_kernel(const float *__restrict__ M,
+                                                     const float *__restrict__ W,
+                                                     float *__restrict__ Bout, uint64_t I, int R,
+                                                     double *__restrict__ BtB, double *__restrict__ dot,
+                                                     const int *__restrict__ done_at, int it) {
+  if (*done_at <= it) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *red = reinterpret_cast<double *>(smraw);          // R*R + R
+  float *w = reinterpret_cast<float *>(red + R * R + R);     // R*R
+  float *mt = w + R * R;                                     // 1024
+  float *ot = mt + 1024;                                     // 1024
+  const int tid = threadIdx.x;
+  const int B = R / 4, BB = B * B, RG = 256 / BB;
+  const int rows = 1024 / R;
+  const int lr = tid / B, c4 = (tid % B) * 4;
+  const int tb = tid % BB, rg = tid / BB, bi = tb / B, bj = tb % B;
+  for (int i = tid; i < R * R + R; i += 256) red[i] = 0.0;
+  for (int i = tid; i < R * R; i += 256) w[i] = W[i];
+  float acc[4][4], dacc_f = 0.f;
+  double dacc[4][4], ddot = 0.0;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      acc[x][y] = 0.f;
+      dacc[x][y] = 0.0;
+    }
+  int steps = 0;
+  const float4 *M4 = reinterpret_cast<const float4 *>(M);
+  float4 *m4 = reinterpret_cast<float4 *>(mt);
+  float4 *o4 = reinterpret_cast<float4 *>(ot);
+  for (uint64_t r0 = (uint64_t)blockIdx.x * rows; r0 < I; r0 += (uint64_t)gridDim.x * rows) {
+    const int nrows = (I - r0) < (uint64_t)rows ? (int)(I - r0) : rows;
+    __syncthreads();
+    if (tid < nrows * B) m4[tid] = M4[r0 * B + tid];
+    __syncthreads();
+    if (lr < nrows) {
+      float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+      const float *mr = mt + lr * R;
+      for (int k = 0; k < R; ++k) {
+        const float mk = mr[k];
+        const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + c4);
+        o0 = fmaf(mk, wk.x, o0);
+        o1 = fmaf(mk, wk.y, o1);
+        o2 = fmaf(mk, wk.z, o2);
+        o3 = fmaf(mk, wk.w, o3);
+      }
+      const float4 o = make_float4(o0, o1, o2, o3);
+      o4[tid] = o;
+      *reinterpret_cast<float4 *>(Bout + (r0 + lr) * (uint64_t)R + c4) = o;
+    }
+    __syncthreads();
+    for (int r = rg; r < nrows; r += RG) {
+      const float4 x = o4[r * B + bi], y = o4[r * B + bj];
+      const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(xa[p], ya[q], acc[p][q]);
+    }
+    if (tid < R)
+      for (int r = 0; r < nrows; ++r) dacc_f = fmaf(mt[r * R + tid], ot[r * R + tid], dacc_f);
+    if (++steps == 32) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          dacc[p][q] += (double)acc[p][q];
+          acc[p][q] = 0.f;
+        }
+      ddot += (double)dacc_f;
+      dacc_f = 0.f;
+      steps = 0;
+    }
   }
   __syncthreads();
-  for (int r = tid; r < R; r += 256) {
-    const double g = Gr[r * R + r];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dacc[p][q] += (double)acc[p][q];
+      atomicAdd(&red[(bi * 4 + p) * R + bj * 4 + q], dacc[p][q]);
+    }
+  if (tid < R) red[R * R + tid] = ddot + (double)dacc_f;
+  __syncthreads();
+  for (int i = tid; i < R * R; i += 256)
+    if (red[i] != 0.0) atomicAdd(&BtB[i], red[i]);
+  for (int i = tid; i < R; i += 256)
+    if (red[R * R + i] != 0.0) atomicAdd(&dot[i], red[R * R + i]);
+}
+
+__global__ void __launch_bounds__(256) finish_kernel(const CpArgs a) {
+  if (*a.done_at <= a.it) return;
+  const int R = a.R, RR = R * R, tid = threadIdx.x;
+  __shared__ double lam[ALTO_MAX_RANK], sn[ALTO_MAX_RANK];
+  __shared__ double part[2][256];
+  double *sv = a.s + (size_t)a.n * R;
+  double *Gn = a.G + (size_t)a.n * RR;
+  for (int r = tid; r < R; r += blockDim.x) {
+    const double g = a.BtB[r * R + r];
     const double l = g > 0.0 ? sqrt(g) : 0.0;
     lam[r] = l;
-    scl[r] = l > 0.0 ? 1.0 / l : 1.0;
+    sn[r] = l > 0.0 ? 1.0 / l : 1.0;
     a.lambda[r] = l;
+    sv[r] = sn[r];
   }
   __syncthreads();
-  for (int e = tid; e < RR; e += 256) {
-    const int i = e / R, j = e % R;
-    a.W[e] = (float)(Vi[e] * scl[j]);
-    a.G_out[e] = Gr[e] * scl[i] * scl[j];
-  }
+  for (int e = tid; e < RR; e += blockDim.x) Gn[e] = a.BtB[e] * sn[e / R] * sn[e % R];
   __syncthreads();
   if (!a.last_mode) return;
-  // fit = 1 - sqrt(max(0, ||X||^2 + lam^T (*_m G_m) lam - 2 <X, X_hat>)) / ||X||
-  // <X, X_hat> = sum_r lam_r sum_i M(i,r) A(i,r) = sum_r lam_r (MtM V^-1)_{rr} scl_r
-  __shared__ double part[2][256];
+  // fit = 1 - sqrt(max(0, ||X||^2 + lam^T (*_m G_m) lam - 2 <X, X_hat>)) / ||X||,
+  // <X, X_hat> = sum_r lam_r sum_i M(i,r) A_n(i,r) = sum_r Sn_r sum_i M_B(i,r) B_n(i,r)
   double s1 = 0.0, s2 = 0.0;
-  for (int e = tid; e < RR; e += 256) {
-    const int i = e / R, j = e % R;
+  for (int e = tid; e < RR; e += blockDim.x) {
     double h = 1.0;
-    for (int m = 0; m < a.N; ++m) h *= (m == a.n) ? a.G_out[e] : a.G[(size_t)m * RR + e];
-    s1 += lam[i] * lam[j] * h;
+    for (int m = 0; m < a.N; ++m) h *= a.G[(size_t)m * RR + e];
+    s1 += lam[e / R] * lam[e % R] * h;
   }
-  for (int r = tid; r < R; r += 256) {
-    double d = 0.0;
-    for (int k = 0; k < R; ++k) d += a.MtM[r * R + k] * Vi[k * R + r];
-    s2 += lam[r] * d * scl[r];
-  }
+  for (int r = tid; r < R; r += blockDim.x) s2 += a.Sn[r] * a.dot[r];
   part[0][tid] = s1;
   part[1][tid] = s2;
   __syncthreads();
@@ -199,38 +290,20 @@ __global__ void __launch_bounds__(256) solve_kernel(const SolveArgs a) {
   }
 }
 
-// A = M W: thread (row, 4 columns), M rows staged in shared memory.
-__global__ void __launch_bounds__(256) rmul_kernel(const float *__restrict__ M, const float *__restrict__ W,
-                                                   float *__restrict__ A, uint64_t I, int R,
-                                                   const int *__restrict__ done_at, int it) {
-  if (done_at && *done_at <= it) return;
-  __shared__ __align__(16) float w[ALTO_MAX_RANK * ALTO_MAX_RANK];
-  __shared__ __align__(16) float m[1024];
-  const int B = R / 4;
-  const int rows = 1024 / R;  // rows per step (256 threads x 4 columns)
-  const int tid = threadIdx.x;
-  for (int i = tid; i < R * R; i += 256) w[i] = W[i];
-  const int lr = tid / B, c4 = (tid % B) * 4;
-  const float4 *M4 = reinterpret_cast<const float4 *>(M);
-  float4 *m4 = reinterpret_cast<float4 *>(m);
-  for (uint64_t r0 = (uint64_t)blockIdx.x * rows; r0 < I; r0 += (uint64_t)gridDim.x * rows) {
-    const int nrows = (I - r0) < (uint64_t)rows ? (int)(I - r0) : rows;
-    __syncthreads();
-    if (tid < nrows * B) m4[tid] = M4[r0 * B + tid];
-    __syncthreads();
-    if (lr < nrows) {
-      float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
-      const float *mr = m + lr * R;
-      for (int k = 0; k < R; ++k) {
-        const float mk = mr[k];
-        const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + c4);
-        o0 = fmaf(mk, wk.x, o0);
-        o1 = fmaf(mk, wk.y, o1);
-        o2 = fmaf(mk, wk.z, o2);
-        o3 = fmaf(mk, wk.w, o3);
-      }
-      *reinterpret_cast<float4 *>(A + (r0 + lr) * (uint64_t)R + c4) = make_float4(o0, o1, o2, o3);
-    }
+__global__ void __launch_bounds__(256) scale_kernel(float *__restrict__ B, const double *__restrict__ s,
+                                                    uint64_t I, int R) {
+  const int per_row = R / 4;
+  const uint64_t total = I * (uint64_t)per_row;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const int c4 = (int)(t % per_row) * 4;
+    float4 *p = reinterpret_cast<float4 *>(B) + t;
+    float4 v = *p;
+    v.x *= (float)s[c4];
+    v.y *= (float)s[c4 + 1];
+    v.z *= (float)s[c4 + 2];
+    v.w *= (float)s[c4 + 3];
+    *p = v;
   }
 }
 
@@ -242,33 +315,59 @@ static int grid_rows(uint64_t I, int rows_per_step, int num_sms, int per_sm) {
   return (int)g;
 }
 
-cudaError_t launch_gram(const float *A, uint64_t I, int R, double *G, const int *done_at, int it,
-                        int num_sms, cudaStream_t s) {
+cudaError_t launch_gram(const float *A, uint64_t I, int R, double *G, int num_sms, cudaStream_t s) {
   if (I == 0) return cudaSuccess;
-  gram_kernel<<<grid_rows(I, kGramRows * 8, num_sms, 4), 256, 0, s>>>(A, I, R, G, done_at, it);
+  gram_kernel<<<grid_rows(I, kGramRows * 8, num_sms, 4), 256, 0, s>>>(A, I, R, G);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s) {
-  const size_t smem = (size_t)(4 * a.R * a.R + 2 * a.R) * sizeof(double);
+cudaError_t launch_prepare(const CpArgs &a, cudaStream_t s) {
   static bool configured = false;
+  const size_t max_smem = (size_t)3 * ALTO_MAX_RANK * ALTO_MAX_RANK * sizeof(double);
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((4 * ALTO_MAX_RANK * ALTO_MAX_RANK + 2 * ALTO_MAX_RANK) *
-                                               sizeof(double)));
+    cudaError_t e = cudaFuncSetAttribute(prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)max_smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  solve_kernel<<<1, 256, smem, s>>>(a);
+  prepare_kernel<<<1, 256, (size_t)3 * a.R * a.R * sizeof(double), s>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rmul(const float *M, const float *W, float *A, uint64_t I, int R,
-                        const int *done_at, int it, int num_sms, cudaStream_t s) {
+static size_t update_smem(int R) {
+  return (size_t)(R * R + R) * sizeof(double) + (size_t)(R * R + 2048) * sizeof(float);
+}
+
+cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, int R, double *BtB,
+                          double *dot, const int *done_at, int it, int num_sms, cudaStream_t s) {
   if (I == 0) return cudaSuccess;
-  rmul_kernel<<<grid_rows(I, 1024 / R, num_sms, 8), 256, 0, s>>>(M, W, A, I, R, done_at, it);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)update_smem(ALTO_MAX_RANK));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  update_kernel<<<grid_rows(I, 1024 / R, num_sms, 2), 256, update_smem(R), s>>>(M, W, B, I, R, BtB,
+                                                                                dot, done_at, it);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const CpArgs &a, cudaStream_t s) {
+  finish_kernel<<<1, 256, 0, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float *B, const double *s_m, uint64_t I, int R, int num_sms, cudaStream_t s) {
+  if (I == 0) return cudaSuccess;
+  const uint64_t total = I * (uint64_t)(R / 4);
+  uint64_t g = (total + 255) / 256;
+  if (g > (uint64_t)num_sms * 16) g = (uint64_t)num_sms * 16;
+  scale_kernel<<<(unsigned)(g ? g : 1), 256, 0, s>>>(B, s_m, I, R);
   note_launches(1);
   return cudaGetLastError();
 }

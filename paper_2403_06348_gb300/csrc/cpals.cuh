@@ -5,26 +5,32 @@
 
 namespace alto {
 
-struct SolveArgs {
-  const double *G;       // [N][R][R] Grams of the current (normalised) factors
-  double *G_out;         // G + n*R*R: overwritten with the new mode-n Gram
-  const double *MtM;     // [R][R] M^T M of this mode's MTTKRP
-  float *W;              // [R][R] out: V^-1 diag(1/lambda), fp32
-  double *lambda;        // [R] out
-  double *fits;          // [iters] fit after each iteration
-  const double *norm_sq; // ||X||^2
-  int *done_at;          // first iteration to skip (early stop); INT_MAX = none
+// Factors are kept internally as B_m with A_m = B_m diag(s_m): the column
+// normalisation of Alg. 1 is carried as the scale vector s_m and folded into
+// the next solve, because MTTKRP commutes with column scaling.
+struct CpArgs {
+  double *G;              // [N][R][R] Grams of the normalised factors A_m
+  double *s;              // [N][R] column scales s_m
+  double *Sn;             // [R] prod_{m != n} s_m of the current mode (kept for the fit)
+  const double *BtB;      // [R][R] B_n^T B_n of the new (unnormalised) update
+  const double *dot;      // [R] sum_i M_B(i, r) B_n(i, r)
+  float *W;               // [R][R] diag(Sn) V^-1 (fp32)
+  double *lambda;         // [R] column norms of the last update
+  double *fits;           // [iters]
+  const double *norm_sq;  // ||X||^2
+  int *done_at;           // first iteration to skip (INT_MAX: none)
   int *iters_done;
   uint32_t *status;
   int N, n, R, it;
-  int last_mode;         // n == N-1: evaluate the fit
+  int last_mode;
   double tol;
 };
 
-cudaError_t launch_gram(const float *A, uint64_t I, int R, double *G, const int *done_at, int it,
-                        int num_sms, cudaStream_t s);
-cudaError_t launch_solve(const SolveArgs &a, cudaStream_t s);
-cudaError_t launch_rmul(const float *M, const float *W, float *A, uint64_t I, int R,
-                        const int *done_at, int it, int num_sms, cudaStream_t s);
+cudaError_t launch_gram(const float *A, uint64_t I, int R, double *G, int num_sms, cudaStream_t s);
+cudaError_t launch_prepare(const CpArgs &a, cudaStream_t s);
+cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, int R, double *BtB,
+                          double *dot, const int *done_at, int it, int num_sms, cudaStream_t s);
+cudaError_t launch_finish(const CpArgs &a, cudaStream_t s);
+cudaError_t launch_scale(float *B, const double *s_m, uint64_t I, int R, int num_sms, cudaStream_t s);
 
 }  // namespace alto

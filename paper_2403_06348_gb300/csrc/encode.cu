@@ -14,14 +14,9 @@ namespace alto {
 template <int KW>
 __global__ void __launch_bounds__(256) linearize_kernel(const __grid_constant__ DecodePlan dp,
                                                         const uint32_t *__restrict__ coords,
-                                                        const float *__restrict__ vals,
                                                         uint64_t nnz, const uint64_t *__restrict__ dims_dev,
                                                         uint64_t *__restrict__ keys,
-                                                        double *__restrict__ norm_sq,
                                                         uint32_t *__restrict__ status) {
-  float acc = 0.f;
-  double dacc = 0.0;
-  int cnt = 0;
   bool bad = false;
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
        x += (uint64_t)gridDim.x * blockDim.x) {
@@ -52,29 +47,98 @@ __global__ void __launch_bounds__(256) linearize_kernel(const __grid_constant__ 
     }
     keys[x * KW] = lo;
     if (KW == 2) keys[x * KW + 1] = hi;
-    const float v = vals[x];
-    acc = fmaf(v, v, acc);
-    if (++cnt == 64) {
-      dacc += (double)acc;
-      acc = 0.f;
-      cnt = 0;
-    }
   }
-  dacc += (double)acc;
   if (bad) atomicOr(status, kStatusCoordRange);
-  // block reduction of the fp64 partial sums
+}
+
+// ---------------------------------------------------------------------------
+// ||X||^2 over cells: after the sort, entries with equal coordinates form runs
+// of equal positions; every run is one cell whose value is the run's sum.
+// norm_runs_kernel: one thread per chunk of kNormChunk entries squares the
+// runs that start and end inside its chunk and leaves the partial sums of runs
+// that cross its edges; norm_span_kernel: the chunk where a crossing run starts
+// adds up the pieces and squares the total.
+// ---------------------------------------------------------------------------
+constexpr int kNormChunk = 32;
+constexpr uint8_t kContLeft = 1, kContRight = 2, kSingleRun = 4;
+
+template <int KW>
+__device__ __forceinline__ bool same_key(const uint64_t *k, uint64_t a, uint64_t b) {
+  if (KW == 1) return k[a] == k[b];
+  return k[2 * a] == k[2 * b] && k[2 * a + 1] == k[2 * b + 1];
+}
+
+__device__ __forceinline__ void block_add_double(double v, double *out) {
   __shared__ double red[32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = dacc;
+  if (lane == 0) red[warp] = v;
   __syncthreads();
   if (warp == 0) {
     double s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && s != 0.0) atomicAdd(norm_sq, s);
+    if (lane == 0 && s != 0.0) atomicAdd(out, s);
   }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) norm_runs_kernel(const uint64_t *__restrict__ keys,
+                                                        const float *__restrict__ vals, uint64_t nnz,
+                                                        uint64_t nchunks, double *__restrict__ head,
+                                                        double *__restrict__ tail,
+                                                        uint8_t *__restrict__ flags,
+                                                        double *__restrict__ norm_sq) {
+  double acc = 0.0;
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t first = c * kNormChunk;
+    const uint64_t last = (first + kNormChunk < nnz ? first + kNormChunk : nnz) - 1;
+    const bool cl = first > 0 && same_key<KW>(keys, first, first - 1);
+    const bool cr = last + 1 < nnz && same_key<KW>(keys, last, last + 1);
+    double run = (double)vals[first], hd = 0.0;
+    bool first_run = true;
+    for (uint64_t x = first + 1; x <= last; ++x) {
+      if (same_key<KW>(keys, x, x - 1)) {
+        run += (double)vals[x];
+      } else {
+        if (first_run && cl)
+          hd = run;
+        else
+          acc += run * run;
+        first_run = false;
+        run = (double)vals[x];
+      }
+    }
+    if (first_run) hd = run;
+    if (!cr && !(first_run && cl)) acc += run * run;
+    head[c] = hd;
+    tail[c] = run;
+    flags[c] = (cl ? kContLeft : 0) | (cr ? kContRight : 0) | (first_run ? kSingleRun : 0);
+  }
+  block_add_double(acc, norm_sq);
+}
+
+__global__ void __launch_bounds__(256) norm_span_kernel(const double *__restrict__ head,
+                                                        const double *__restrict__ tail,
+                                                        const uint8_t *__restrict__ flags,
+                                                        uint64_t nchunks, double *__restrict__ norm_sq) {
+  double acc = 0.0;
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+       c += (uint64_t)gridDim.x * blockDim.x) {
+    const uint8_t f = flags[c];
+    if ((f & kContRight) && !((f & kSingleRun) && (f & kContLeft))) {
+      double S = tail[c];
+      for (uint64_t k = c + 1; k < nchunks; ++k) {
+        const uint8_t fk = flags[k];
+        S += head[k];
+        if (!((fk & kSingleRun) && (fk & kContRight))) break;
+      }
+      acc += S * S;
+    }
+  }
+  block_add_double(acc, norm_sq);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,16 +553,32 @@ static int grid_for(uint64_t work, int threads, int max_blocks) {
   return (int)b;
 }
 
-cudaError_t launch_linearize(const DecodePlan &dp, const uint32_t *coords, const float *vals,
-                             uint64_t nnz, const uint64_t *dims_dev, uint64_t *keys,
-                             double *norm_sq, uint32_t *status, int num_sms, cudaStream_t s) {
+cudaError_t launch_linearize(const DecodePlan &dp, const uint32_t *coords, uint64_t nnz,
+                             const uint64_t *dims_dev, uint64_t *keys, uint32_t *status, int num_sms,
+                             cudaStream_t s) {
   if (nnz == 0) return cudaSuccess;
   const int grid = grid_for(nnz, 256, num_sms * 8);
   if (dp.kw == 1)
-    linearize_kernel<1><<<grid, 256, 0, s>>>(dp, coords, vals, nnz, dims_dev, keys, norm_sq, status);
+    linearize_kernel<1><<<grid, 256, 0, s>>>(dp, coords, nnz, dims_dev, keys, status);
   else
-    linearize_kernel<2><<<grid, 256, 0, s>>>(dp, coords, vals, nnz, dims_dev, keys, norm_sq, status);
+    linearize_kernel<2><<<grid, 256, 0, s>>>(dp, coords, nnz, dims_dev, keys, status);
   note_launches(1);
+  return cudaGetLastError();
+}
+
+uint64_t norm_chunks(uint64_t nnz) { return (nnz + kNormChunk - 1) / kNormChunk; }
+
+cudaError_t launch_norm(int kw, const uint64_t *keys, const float *vals, uint64_t nnz, double *head,
+                        double *tail, uint8_t *flags, double *norm_sq, int num_sms, cudaStream_t s) {
+  if (nnz == 0) return cudaSuccess;
+  const uint64_t nc = norm_chunks(nnz);
+  const int grid = grid_for(nc, 256, num_sms * 8);
+  if (kw == 1)
+    norm_runs_kernel<1><<<grid, 256, 0, s>>>(keys, vals, nnz, nc, head, tail, flags, norm_sq);
+  else
+    norm_runs_kernel<2><<<grid, 256, 0, s>>>(keys, vals, nnz, nc, head, tail, flags, norm_sq);
+  norm_span_kernel<<<grid, 256, 0, s>>>(head, tail, flags, nc, norm_sq);
+  note_launches(2);
   return cudaGetLastError();
 }
 

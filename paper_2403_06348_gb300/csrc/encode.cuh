@@ -5,9 +5,14 @@
 
 namespace alto {
 
-cudaError_t launch_linearize(const DecodePlan &dp, const uint32_t *coords, const float *vals,
-                             uint64_t nnz, const uint64_t *dims_dev, uint64_t *keys,
-                             double *norm_sq, uint32_t *status, int num_sms, cudaStream_t s);
+cudaError_t launch_linearize(const DecodePlan &dp, const uint32_t *coords, uint64_t nnz,
+                             const uint64_t *dims_dev, uint64_t *keys, uint32_t *status, int num_sms,
+                             cudaStream_t s);
+
+// ||X||^2 with duplicate positions summed into one cell (keys must be sorted).
+uint64_t norm_chunks(uint64_t nnz);
+cudaError_t launch_norm(int kw, const uint64_t *keys, const float *vals, uint64_t nnz, double *head,
+                        double *tail, uint8_t *flags, double *norm_sq, int num_sms, cudaStream_t s);
 
 size_t sort_table_entries(uint64_t nnz);
 size_t sort_scan_blocks(uint64_t nnz);

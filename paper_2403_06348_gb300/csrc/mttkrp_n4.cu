@@ -1,0 +1,6 @@
+// MTTKRP segment kernels specialised for 4 modes.
+#include "mttkrp_kernel.cuh"
+
+namespace alto {
+template cudaError_t launch_mttkrp_nt<4>(const MttkrpArgs &, int, bool, bool, size_t, int, cudaStream_t);
+}  // namespace alto

@@ -39,6 +39,21 @@ def test_fit_trajectory_matches_oracle(R):
     np.testing.assert_allclose(lam, ref.lam, rtol=1e-2)
 
 
+def test_fit_trajectory_zipf_skewed():
+    """Zipf heads make the columns of M nearly collinear in early iterations;
+    the fit and lambda must still follow the fp64 oracle."""
+    spec = synth.scaled(synth.CONFIGS[1], 300_000, dims=(200_000, 40_000, 5_000))
+    coords, vals = synth.generate(spec)
+    R = 16
+    init = gu.rand_factors(spec.dims, R, 11)
+    ref = _oracle_cpals(coords, vals, spec.dims, init, iters=4)
+    t = gu.encode(coords, vals, spec.dims)
+    A = gu.gpu_factors(init)
+    lam, fits = t.cpals(R, 4, A)
+    np.testing.assert_allclose(fits, ref.fits, atol=1e-4)
+    np.testing.assert_allclose(np.sort(lam), np.sort(ref.lam), rtol=1e-2)
+
+
 def test_exact_low_rank_recovered():
     """An exact rank-4 tensor decomposed at R = 4 reaches fit 1 (up to fp32)."""
     rng = np.random.default_rng(1)
@@ -51,7 +66,12 @@ def test_exact_low_rank_recovered():
     t = gu.encode(coords, vals, dims)
     A = gu.gpu_factors([np.random.default_rng(2).random((d, R)).astype(np.float32) for d in dims])
     lam, fits = t.cpals(R, 150, A)
-    assert fits[-1] > 1 - 1e-4
+    # The fit is evaluated from fp32 MTTKRP output through the expansion
+    # ||X||^2 + ||X_hat||^2 - 2<X, X_hat>, whose cancellation limits it to about
+    # sqrt(fp32 epsilon) near 1; the model itself is checked directly in fp64.
+    assert fits[-1] > 1 - 1e-3
+    Xh = ar.reconstruct_dense(lam, [a.double().cpu().numpy() for a in A])
+    assert np.linalg.norm(X - Xh) / np.linalg.norm(X) < 1e-4
 
 
 def test_tol_stops_early_and_host_factors_match_device():

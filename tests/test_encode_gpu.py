@@ -39,8 +39,8 @@ def _check(coords, vals, dims, L=None, host=False):
         dc, dv = t.decode()
         np.testing.assert_array_equal(dc.cpu().numpy().view(np.uint32),
                                       ar.delinearize(ref.lo, ref.hi, ref.plan))
-    norm = float(np.sum(vals.astype(np.float64) ** 2))
-    assert abs(info.norm_sq - norm) <= 1e-6 * max(norm, 1.0)
+    norm = ar.tensor_norm_sq(coords, vals)
+    assert abs(info.norm_sq - norm) <= 1e-9 * max(norm, 1.0)
     if L is not None:
         t.set_partitions(L)
     starts, iv = t.partition()
