@@ -17,7 +17,9 @@ from typing import List, Optional, Sequence, Tuple
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_build", "libalto.so")
+# ALTO_LIB points the binding at another build of the library (e.g. a tuning
+# variant); by default the in-tree build is used.
+LIB_PATH = os.environ.get("ALTO_LIB") or os.path.join(_PKG, "_build", "libalto.so")
 
 ALTO_MAX_MODES = 8
 ALTO_MAX_HOT = 4096

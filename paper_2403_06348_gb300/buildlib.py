@@ -47,15 +47,19 @@ def _stale(target: str, deps: List[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: Optional[List[str]] = None) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: Optional[List[str]] = None,
+          out_dir: Optional[str] = None) -> str:
+    """Compile csrc/*.cu into <out_dir>/libalto.so (default: the package's _build)."""
+    out = out_dir or OUT_DIR
+    lib = os.path.join(out, "libalto.so")
+    os.makedirs(out, exist_ok=True)
     srcs = sources()
     headers = _deps()
     objs = []
     jobs = []
     flags = NVCC_FLAGS + (extra or [])
     for src in srcs:
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([nvcc(), *ARCH, *flags, "-c", src, "-o", obj])
@@ -70,11 +74,11 @@ def build(force: bool = False, verbose: bool = False, extra: Optional[List[str]]
     if jobs:
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

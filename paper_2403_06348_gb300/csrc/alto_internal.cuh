@@ -38,6 +38,48 @@ struct DecodePlan {
   BitRun runs[kMaxModes][kMaxRuns];
 };
 
+// The bit plan by blocks (Section III-A): sort the modes by length (rank 0 =
+// shortest); block j holds the bit groups g with bits(rank j-1) <= g <
+// bits(rank j), each group holding bit g of ranks j..N-1 in rank order, so
+// block j is an (N - j)-way interleave and bit g of rank q >= j sits at
+// base[j] + (g - off[j]) * (N - j) + (q - j). Decoding rank q therefore takes,
+// for every block j <= q, a window starting at base[j] + q - j, keeps cnt[j]
+// bits at stride N - j (mask[j]) and compacts them with a stride known at
+// compile time. A block wider than 64 bits (two-word positions) is cut in two
+// windows: the second starts shift2[j] bits later and holds cnt2[j] bits.
+struct BlockPlan {
+  int nmodes;
+  int kw;
+  int out_rank;                 // rank of the MTTKRP output mode
+  uint8_t base[kMaxModes];
+  uint8_t off[kMaxModes];       // coordinate bit of the block's first bit
+  uint8_t shift2[kMaxModes];
+  uint8_t off2[kMaxModes];
+  uint64_t mask[kMaxModes];     // cnt[j] bits at stride N - j from bit 0
+  uint64_t mask2[kMaxModes];    // second window (0 if none)
+};
+
+// The same bit plan cut into runs that fit a 32-bit window, with the masks
+// and shifts of the compaction precomputed on the host: the run's bits sit at
+// window bits 0, k, 2k, ... (count of them); x = window & mask[0], then for
+// each step j, x = (x | x >> sh[j]) & mask[j + 1] doubles the packed groups.
+constexpr int kMaxRuns32 = 16;
+struct Run32 {
+  uint32_t mask[6];
+  uint8_t sh[5];
+  uint8_t start;     // key bit of the first bit of the run
+  uint8_t steps;     // number of doubling steps
+  uint8_t outshift;  // coordinate bit of the first bit of the run
+};
+
+struct DecodePlan32 {
+  int nmodes;
+  int kw;
+  int nruns[kMaxModes];
+  Run32 runs[kMaxModes][kMaxRuns32];
+};
+
+
 // ---------------------------------------------------------------------------
 // Stride compaction (PEXT of a regularly spaced mask) and expansion (PDEP).
 // For stride K the bits at 0, K, 2K, ... are gathered into consecutive bits by
@@ -115,11 +157,34 @@ __device__ __forceinline__ uint64_t expand_stride(uint64_t v, int k, int cnt) {
   }
 }
 
+// Gathers bits 0, K, 2K, ... of x (already masked to those positions) into
+// the low bits: fixed doubling steps with immediate masks.
+template <int K>
+__device__ __forceinline__ uint64_t compact_fixed(uint64_t x) {
+  if constexpr (K == 1) {
+    return x;
+  } else {
+    constexpr int kMaxCnt = (63 / K + 1) < 32 ? (63 / K + 1) : 32;
+    if constexpr (kMaxCnt > 1) x = (x | shr_c<(K - 1) << 0>(x)) & stride_mask(K, 1);
+    if constexpr (kMaxCnt > 2) x = (x | shr_c<(K - 1) << 1>(x)) & stride_mask(K, 2);
+    if constexpr (kMaxCnt > 4) x = (x | shr_c<(K - 1) << 2>(x)) & stride_mask(K, 3);
+    if constexpr (kMaxCnt > 8) x = (x | shr_c<(K - 1) << 3>(x)) & stride_mask(K, 4);
+    if constexpr (kMaxCnt > 16) x = (x | shr_c<(K - 1) << 4>(x)) & stride_mask(K, 5);
+    return x;
+  }
+}
+
 // 64-bit window of a 128-bit position starting at bit s.
 __device__ __forceinline__ uint64_t window64(uint64_t lo, uint64_t hi, int s) {
   if (s == 0) return lo;
   if (s < 64) return (lo >> s) | (hi << (64 - s));
   return hi >> (s - 64);
+}
+
+template <int KW>
+__device__ __forceinline__ uint32_t window32(uint64_t lo, uint64_t hi, int s) {
+  if (KW == 1) return (uint32_t)(lo >> s);
+  return (uint32_t)window64(lo, hi, s);
 }
 
 // De-linearize one position into all coordinates (EXTRACT of Alg. 3).

@@ -76,6 +76,10 @@ struct alto_tensor {
   int bits[kMaxModes] = {};
   uint64_t mask_lo[kMaxModes] = {}, mask_hi[kMaxModes] = {};
   DecodePlan dp{};
+  DecodePlan32 dp32{};
+  BlockPlan bp{};
+  int rank_of[kMaxModes] = {};   // rank (order by length) of each mode
+  int mode_of[kMaxModes] = {};   // mode of each rank
   alto_allocator alloc{};
   bool user_alloc = false;
   cudaStream_t stream = nullptr;
@@ -241,6 +245,72 @@ alto_status build_bit_plan(alto_tensor *h) {
     }
     dp.nruns[n] = nr;
   }
+  // 32-bit runs with precomputed compaction masks (the MTTKRP decode)
+  DecodePlan32 &d32 = h->dp32;
+  memset(&d32, 0, sizeof(d32));
+  d32.nmodes = N;
+  d32.kw = h->kw;
+  for (int n = 0; n < N; ++n) {
+    int nr = 0, g = 0;
+    while (g < h->bits[n]) {
+      const int start = pos[n][g];
+      int k = 1, cnt = 1;
+      if (g + 1 < h->bits[n] && pos[n][g + 1] - start < 32) {
+        k = pos[n][g + 1] - start;
+        cnt = 2;
+        while (g + cnt < h->bits[n] && pos[n][g + cnt] - pos[n][g + cnt - 1] == k &&
+               pos[n][g + cnt] - start < 32)
+          ++cnt;
+      }
+      if (nr >= kMaxRuns32) return fail(ALTO_ERR_UNSUPPORTED, "bit plan needs too many runs");
+      Run32 &r = d32.runs[n][nr++];
+      r.start = (uint8_t)start;
+      r.outshift = (uint8_t)g;
+      int steps = 0;
+      while ((1 << steps) < cnt) ++steps;
+      r.steps = (uint8_t)steps;
+      uint32_t m0 = 0;
+      for (int t = 0; t < cnt; ++t) m0 |= 1u << (k * t);
+      r.mask[0] = m0;
+      for (int j = 0; j < steps; ++j) {
+        r.sh[j] = (uint8_t)((k - 1) << j);
+        // after step j: groups of 2^(j+1) bits at multiples of k * 2^(j+1)
+        uint32_t m = 0;
+        const int gsz = 1 << (j + 1), sp = k * gsz;
+        for (int p = 0; p < 32; p += sp)
+          for (int b = 0; b < gsz && p + b < 32; ++b) m |= 1u << (p + b);
+        r.mask[j + 1] = m;
+      }
+      g += cnt;
+    }
+    d32.nruns[n] = nr;
+  }
+  // the block view of the same plan (Section III-A), ranks = modes by length
+  BlockPlan &bp = h->bp;
+  memset(&bp, 0, sizeof(bp));
+  bp.nmodes = N;
+  bp.kw = h->kw;
+  for (int q = 0; q < N; ++q) {
+    h->mode_of[q] = order[q];
+    h->rank_of[order[q]] = q;
+  }
+  int base = 0, prev_bits = 0;
+  for (int j = 0; j < N; ++j) {
+    const int k = N - j;
+    const int cnt = h->bits[order[j]] - prev_bits;
+    bp.base[j] = (uint8_t)base;
+    bp.off[j] = (uint8_t)prev_bits;
+    const int h1 = std::min(cnt, 63 / k + 1);
+    for (int t = 0; t < h1; ++t) bp.mask[j] |= 1ull << (k * t);
+    if (cnt > h1) {
+      bp.shift2[j] = (uint8_t)(h1 * k);
+      bp.off2[j] = (uint8_t)(prev_bits + h1);
+      for (int t = 0; t < cnt - h1; ++t) bp.mask2[j] |= 1ull << (k * t);
+      if (h->kw == 1) return fail(ALTO_ERR_UNSUPPORTED, "internal: block wider than 64 bits");
+    }
+    base += cnt * k;
+    prev_bits = h->bits[order[j]];
+  }
   return ALTO_OK;
 }
 
@@ -379,8 +449,7 @@ alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) 
 
 bool rank_ok(int R) { return R == 4 || R == 8 || R == 16 || R == 32 || R == 64; }
 
-// Shared memory budget of the staged tables: one persistent CTA per SM.
-size_t stage_budget() { return mttkrp_smem_limit() - 1024; }
+size_t stage_budget() { return mttkrp_stage_budget(); }
 
 int hot_slots_that_fit(int R, int want) {
   const size_t budget = stage_budget();
@@ -396,14 +465,13 @@ int hot_slots_that_fit(int R, int want) {
 
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   alto_mode_plan p = h->plan[mode];
-  if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16)
-    p.cols_per_lane = (R % 8 == 0) ? 8 : 4;
+  if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16) p.cols_per_lane = 4;
   while (R % p.cols_per_lane) p.cols_per_lane /= 2;
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
-  const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
+  const bool pull_fits = pull_smem <= stage_budget() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
     const double reuse = (double)h->M / (double)h->dims[mode];
-    p.variant = (reuse > 4.0 && pull_fits && pull_smem <= stage_budget()) ? ALTO_VARIANT_PULL
+    p.variant = (reuse > 4.0 && pull_fits) ? ALTO_VARIANT_PULL
                                                                            : ALTO_VARIANT_ATOMIC;
   }
   if (p.variant == ALTO_VARIANT_PULL && !pull_fits)
@@ -432,17 +500,17 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
   if (st != ALTO_OK) return st;
   const uint64_t I = h->dims[mode];
   MttkrpArgs a{};
-  // coordinate 0 of the kernel's decode is the output mode
-  int order[kMaxModes];
-  order[0] = mode;
-  for (int m = 0, j = 1; m < h->N; ++m)
-    if (m != mode) order[j++] = m;
+  // the kernel works on coordinates in rank order (modes sorted by length)
+  a.bp = h->bp;
+  a.bp.out_rank = h->rank_of[mode];
+  a.out_rank = h->rank_of[mode];
   a.dp.nmodes = h->N;
   a.dp.kw = h->kw;
-  for (int j = 0; j < h->N; ++j) {
-    a.dp.nruns[j] = h->dp.nruns[order[j]];
-    memcpy(a.dp.runs[j], h->dp.runs[order[j]], sizeof(a.dp.runs[j]));
-    a.factors[j] = j ? factors[order[j]] : nullptr;
+  for (int q = 0; q < h->N; ++q) {
+    const int m = h->mode_of[q];
+    a.dp.nruns[q] = h->dp32.nruns[m];
+    memcpy(a.dp.runs[q], h->dp32.runs[m], sizeof(a.dp.runs[q]));
+    a.factors[q] = m == mode ? nullptr : factors[m];
   }
   a.keys = h->keys;
   a.vals = h->vals;

@@ -151,94 +151,129 @@ __global__ void __launch_bounds__(256) prepare_kernel(const CpArgs a) {
 }
 
 // B = M W with B^T B and the column dot products of M and B, one pass.
-__global__ void __launch_bounds__(256) update_kernel(const float *__restrict__ M,
-                                                     const float *__restrict__ W,
-                                                     float *__restrict__ Bout, uint64_t I, int R,
-                                                     double *__restrict__ BtB, double *__restrict__ dot,
-                                                     const int *__restrict__ done_at, int it) {
+// A tile of TR = 4096 / R rows: every thread computes a 4-row x 4-column block
+// of B from the transposed M tile and W (two 16-byte shared loads per 16
+// FMAs), adds its block's column products M(r,c) B(r,c), stores B, and then
+// accumulates a 4 x 4 block of B^T B over its share of the tile's rows.
+// fp32 partial sums cover at most 32 tiles per thread before they move to
+// fp64.
+constexpr int kUpdThreads = 256;
+
+__global__ void __launch_bounds__(kUpdThreads) update_kernel(const float *__restrict__ M,
+                                                             const float *__restrict__ W,
+                                                             float *__restrict__ Bout, uint64_t I, int R,
+                                                             double *__restrict__ BtB, double *__restrict__ dot,
+                                                             const int *__restrict__ done_at, int it) {
   if (*done_at <= it) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double *red = reinterpret_cast<double *>(smraw);          // R*R + R
-  float *w = reinterpret_cast<float *>(red + R * R + R);     // R*R
-  float *mt = w + R * R;                                     // 1024
-  float *ot = mt + 1024;                                     // 1024
+  const int TR = 4096 / R;       // rows per tile
+  const int TRP = TR + 4;        // padded row count of the transposed tile
+  const int RP = R + 4;          // padded row length of the B tile
+  double *red = reinterpret_cast<double *>(smraw);       // R*R + R
+  float *w = reinterpret_cast<float *>(red + R * R + R);  // R*R
+  float *mt = w + R * R;                                  // R * TRP (M tile, transposed)
+  float *bt = mt + R * TRP;                               // TR * RP (B tile)
   const int tid = threadIdx.x;
-  const int B = R / 4, BB = B * B, RG = 256 / BB;
-  const int rows = 1024 / R;
-  const int lr = tid / B, c4 = (tid % B) * 4;
-  const int tb = tid % BB, rg = tid / BB, bi = tb / B, bj = tb % B;
-  for (int i = tid; i < R * R + R; i += 256) red[i] = 0.0;
-  for (int i = tid; i < R * R; i += 256) w[i] = W[i];
-  float acc[4][4], dacc_f = 0.f;
-  double dacc[4][4], ddot = 0.0;
+  const int B4 = R / 4;                      // column blocks
+  const int cb = tid % B4, rb = tid / B4;    // phase 1: rows 4*rb .. 4*rb+3, cols 4*cb ..
+  const int BB = B4 * B4, RG = kUpdThreads / BB;
+  const int tb = tid % BB, rg = tid / BB, bi = tb / B4, bj = tb % B4;
+  for (int i = tid; i < R * R + R; i += kUpdThreads) red[i] = 0.0;
+  for (int i = tid; i < R * R; i += kUpdThreads) w[i] = W[i];
+  float g[4][4], dp[4];
+  double dg[4][4], ddp[4];
 #pragma unroll
-  for (int x = 0; x < 4; ++x)
+  for (int x = 0; x < 4; ++x) {
+    dp[x] = 0.f;
+    ddp[x] = 0.0;
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-      acc[x][y] = 0.f;
-      dacc[x][y] = 0.0;
+      g[x][y] = 0.f;
+      dg[x][y] = 0.0;
     }
-  int steps = 0;
+  }
+  int tiles = 0;
   const float4 *M4 = reinterpret_cast<const float4 *>(M);
-  float4 *m4 = reinterpret_cast<float4 *>(mt);
-  float4 *o4 = reinterpret_cast<float4 *>(ot);
-  for (uint64_t r0 = (uint64_t)blockIdx.x * rows; r0 < I; r0 += (uint64_t)gridDim.x * rows) {
-    const int nrows = (I - r0) < (uint64_t)rows ? (int)(I - r0) : rows;
+  for (uint64_t r0 = (uint64_t)blockIdx.x * TR; r0 < I; r0 += (uint64_t)gridDim.x * TR) {
+    const int nrows = (I - r0) < (uint64_t)TR ? (int)(I - r0) : TR;
     __syncthreads();
-    if (tid < nrows * B) m4[tid] = M4[r0 * B + tid];
+    // transpose the M tile into shared memory (rows beyond nrows are zero)
+    for (int i = tid; i < TR * B4; i += kUpdThreads) {
+      const int r = i / B4, c = (i - r * B4) * 4;
+      const float4 m = r < nrows ? M4[(r0 + r) * B4 + (i - r * B4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+      mt[(c + 0) * TRP + r] = m.x;
+      mt[(c + 1) * TRP + r] = m.y;
+      mt[(c + 2) * TRP + r] = m.z;
+      mt[(c + 3) * TRP + r] = m.w;
+    }
     __syncthreads();
-    if (lr < nrows) {
-      float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
-      const float *mr = mt + lr * R;
-      for (int k = 0; k < R; ++k) {
-        const float mk = mr[k];
-        const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + c4);
-        o0 = fmaf(mk, wk.x, o0);
-        o1 = fmaf(mk, wk.y, o1);
-        o2 = fmaf(mk, wk.z, o2);
-        o3 = fmaf(mk, wk.w, o3);
-      }
-      const float4 o = make_float4(o0, o1, o2, o3);
-      o4[tid] = o;
-      *reinterpret_cast<float4 *>(Bout + (r0 + lr) * (uint64_t)R + c4) = o;
+    float o[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
+    for (int k = 0; k < R; ++k) {
+      const float4 mk = *reinterpret_cast<const float4 *>(mt + k * TRP + 4 * rb);
+      const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + 4 * cb);
+      const float ma[4] = {mk.x, mk.y, mk.z, mk.w}, wa[4] = {wk.x, wk.y, wk.z, wk.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o[x][y] = fmaf(ma[x], wa[y], o[x][y]);
+    }
+    // column products with M, store B (global and shared)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const float4 mc = *reinterpret_cast<const float4 *>(mt + (4 * cb + y) * TRP + 4 * rb);
+      const float ma[4] = {mc.x, mc.y, mc.z, mc.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x) dp[y] = fmaf(ma[x], o[x][y], dp[y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int r = 4 * rb + x;
+      const float4 ov = make_float4(o[x][0], o[x][1], o[x][2], o[x][3]);
+      *reinterpret_cast<float4 *>(bt + r * RP + 4 * cb) = ov;
+      if (r < nrows) *reinterpret_cast<float4 *>(Bout + (r0 + r) * (uint64_t)R + 4 * cb) = ov;
     }
     __syncthreads();
     for (int r = rg; r < nrows; r += RG) {
-      const float4 x = o4[r * B + bi], y = o4[r * B + bj];
-      const float xa[4] = {x.x, x.y, x.z, x.w}, ya[4] = {y.x, y.y, y.z, y.w};
+      const float4 xv = *reinterpret_cast<const float4 *>(bt + r * RP + 4 * bi);
+      const float4 yv = *reinterpret_cast<const float4 *>(bt + r * RP + 4 * bj);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(xa[p], ya[q], acc[p][q]);
+        for (int y = 0; y < 4; ++y) g[x][y] = fmaf(xa[x], ya[y], g[x][y]);
     }
-    if (tid < R)
-      for (int r = 0; r < nrows; ++r) dacc_f = fmaf(mt[r * R + tid], ot[r * R + tid], dacc_f);
-    if (++steps == 32) {
+    if (++tiles == 32) {
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int x = 0; x < 4; ++x) {
+        ddp[x] += (double)dp[x];
+        dp[x] = 0.f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          dacc[p][q] += (double)acc[p][q];
-          acc[p][q] = 0.f;
+        for (int y = 0; y < 4; ++y) {
+          dg[x][y] += (double)g[x][y];
+          g[x][y] = 0.f;
         }
-      ddot += (double)dacc_f;
-      dacc_f = 0.f;
-      steps = 0;
+      }
+      tiles = 0;
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
+  for (int x = 0; x < 4; ++x) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      dacc[p][q] += (double)acc[p][q];
-      atomicAdd(&red[(bi * 4 + p) * R + bj * 4 + q], dacc[p][q]);
+    for (int y = 0; y < 4; ++y) {
+      dg[x][y] += (double)g[x][y];
+      atomicAdd(&red[(4 * bi + x) * R + 4 * bj + y], dg[x][y]);
     }
-  if (tid < R) red[R * R + tid] = ddot + (double)dacc_f;
+    atomicAdd(&red[R * R + 4 * cb + x], ddp[x] + (double)dp[x]);
+  }
   __syncthreads();
-  for (int i = tid; i < R * R; i += 256)
+  for (int i = tid; i < R * R; i += kUpdThreads)
     if (red[i] != 0.0) atomicAdd(&BtB[i], red[i]);
-  for (int i = tid; i < R; i += 256)
+  for (int i = tid; i < R; i += kUpdThreads)
     if (red[R * R + i] != 0.0) atomicAdd(&dot[i], red[R * R + i]);
 }
 
@@ -337,7 +372,9 @@ cudaError_t launch_prepare(const CpArgs &a, cudaStream_t s) {
 }
 
 static size_t update_smem(int R) {
-  return (size_t)(R * R + R) * sizeof(double) + (size_t)(R * R + 2048) * sizeof(float);
+  const int TR = 4096 / R;
+  return (size_t)(R * R + R) * sizeof(double) +
+         (size_t)(R * R + R * (TR + 4) + TR * (R + 4)) * sizeof(float);
 }
 
 cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, int R, double *BtB,
@@ -350,8 +387,10 @@ cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, 
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  update_kernel<<<grid_rows(I, 1024 / R, num_sms, 2), 256, update_smem(R), s>>>(M, W, B, I, R, BtB,
-                                                                                dot, done_at, it);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, update_kernel, kUpdThreads, update_smem(R));
+  update_kernel<<<grid_rows(I, 4096 / R, num_sms, per_sm > 0 ? per_sm : 1), kUpdThreads,
+                  update_smem(R), s>>>(M, W, B, I, R, BtB, dot, done_at, it);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -45,6 +45,17 @@ size_t mttkrp_smem_limit() {
   return (size_t)v;
 }
 
+size_t mttkrp_stage_budget() {
+  static int per_sm = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  }
+  size_t b = (size_t)per_sm / kMttkrpBlocksPerSm - 2048;
+  return b < mttkrp_smem_limit() ? b : mttkrp_smem_limit();
+}
+
 cudaError_t launch_mttkrp(const MttkrpArgs &a, int cpl, bool bf16, bool pull, size_t smem,
                           int num_sms, cudaStream_t s) {
   if (a.nnz == 0) return cudaSuccess;

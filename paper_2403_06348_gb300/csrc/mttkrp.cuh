@@ -5,18 +5,29 @@
 
 namespace alto {
 
-constexpr int kMttkrpThreads = 1024;  // one persistent CTA per SM
+// Persistent CTAs: kMttkrpBlocksPerSm CTAs of kMttkrpThreads threads per SM.
+#ifndef ALTO_MTTKRP_THREADS
+#define ALTO_MTTKRP_THREADS 1024
+#endif
+#ifndef ALTO_MTTKRP_BLOCKS_PER_SM
+#define ALTO_MTTKRP_BLOCKS_PER_SM 1
+#endif
+constexpr int kMttkrpThreads = ALTO_MTTKRP_THREADS;
+constexpr int kMttkrpBlocksPerSm = ALTO_MTTKRP_BLOCKS_PER_SM;
 
+// Coordinates inside the kernel are in rank order (modes sorted by length).
 struct MttkrpArgs {
-  DecodePlan dp;               // permuted: coordinate 0 is the output mode
+  BlockPlan bp;                // decode by blocks (kernels specialised on N)
+  DecodePlan32 dp;             // decode by 32-bit runs, rows in rank order (any N)
   const uint64_t *keys;        // ordered positions [nnz][kw]
   const float *vals;           // ordered values [nnz]
   uint64_t nnz;
   uint64_t L;                  // line segments
   const uint32_t *intervals;   // [L][N][2] (original mode order)
-  const void *factors[kMaxModes];  // permuted like dp; factors[0] unused
+  const void *factors[kMaxModes];  // by rank; the output rank's entry is unused
   float *out;                  // [I_mode][R]
   int mode;                    // output mode in the original order
+  int out_rank;                // its rank
   int R;
   int flush_every;             // ATOMIC: segments between flushes of the hot table
   // ATOMIC variant: hot rows staged in shared memory
@@ -34,6 +45,9 @@ size_t mttkrp_smem_bytes(bool pull, int R, int nslots, int hbits, uint32_t max_i
 
 // Largest dynamic shared memory a block may use on this device.
 size_t mttkrp_smem_limit();
+
+// Shared memory one segment-kernel CTA may use for its staging table.
+size_t mttkrp_stage_budget();
 
 // cpl = factor columns per lane (R / cpl lanes work on one nonzero).
 cudaError_t launch_mttkrp(const MttkrpArgs &a, int cpl, bool bf16, bool pull, size_t smem,
