@@ -196,6 +196,36 @@ alto_status alto_mttkrp(alto_handle_t h, int mode, const void *const *factors,
                         alto_dtype fdtype, int R, float *out, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * alto_mttkrp_noalloc -- the same MTTKRP as alto_mttkrp with the PULL
+ * variant, for callers that cannot have the library allocate device memory
+ * while they run (for example a service that reserved its whole device budget
+ * at start-up, or a framework whose own allocator must see every device
+ * allocation). The paper has no counterpart: it is an interface addition.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine. The segments'
+ * partials live in one fixed device array of 8 Mi floats (32 MiB) inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. The first call on a device looks up that array's device address;
+ * make that first call before any stream capture.
+ *
+ * Arguments are those of alto_mttkrp. Requirements, each checked:
+ *  - the mode's row-to-segment lists must already exist: one earlier
+ *    alto_mttkrp call on this mode with the PULL variant (alto_set_mode_plan)
+ *    builds them, and that call may allocate;
+ *  - the largest mode interval times R must fit shared memory;
+ *  - sum over segments of (interval length) * R <= 8 Mi floats.
+ * Errors: INVALID_ARG (bad arguments, lists not built), UNSUPPORTED (rank,
+ * shared memory, or the fixed scratch too small, with the sizes in the
+ * message), CUDA.
+ * All calls share the one scratch array: calls that overlap on the GPU (two
+ * streams, or two host threads) race and give wrong results. Nothing in the
+ * array needs clearing between calls: every segment rewrites its whole part
+ * before the reduction reads it.
+ * ------------------------------------------------------------------------- */
+alto_status alto_mttkrp_noalloc(alto_handle_t h, int mode, const void *const *factors,
+                                alto_dtype fdtype, int R, float *out, void *stream);
+
+/* ---------------------------------------------------------------------------
  * cpals_run -- CP-ALS, Alg. 1: for each iteration and each mode n:
  * V = Hadamard product of the Grams G_m = A^(m)T A^(m), m != n (fp64);
  * M = MTTKRP (alto_mttkrp); A^(n) = M V^-1 through a Cholesky factorisation of

@@ -85,6 +85,7 @@ SIGNATURES = {
     "alto_mttkrp": ([_vp, _i32, _vp, _i32, _i32, _vp, _vp], _i32),
     "cpals_run": ([_vp, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_i32), _vp],
                   _i32),
+    "alto_mttkrp_noalloc": ([_vp, _i32, _vp, _i32, _i32, _vp, _vp], _i32),
     "alto_profile_enable": ([_vp, _i32], _i32),
     "alto_profile_read": ([_vp, ctypes.POINTER(alto_profile), _i32], _i32),
     "alto_kernel_launches": ([], _u64),
@@ -188,6 +189,15 @@ def alto_mttkrp(t: "AltoTensor", mode: int, factors, R: int, out, dtype: int = A
     arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
     _check(lib().alto_mttkrp(t.handle, int(mode), arr, int(dtype), int(R), _ptr(out),
                              _stream_ptr(stream)))
+
+
+def alto_mttkrp_noalloc(t: "AltoTensor", mode: int, factors, R: int, out, dtype: int = ALTO_F32,
+                        stream=None) -> None:
+    """Pull-variant MTTKRP that allocates nothing (scratch in the library's fixed
+    device array); the mode's pull lists must exist (see include/alto.h)."""
+    arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
+    _check(lib().alto_mttkrp_noalloc(t.handle, int(mode), arr, int(dtype), int(R), _ptr(out),
+                                     _stream_ptr(stream)))
 
 
 def cpals_run(t: "AltoTensor", R: int, iters: int, factors, lam, fits: Optional[np.ndarray] = None,

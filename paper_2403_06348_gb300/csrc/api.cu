@@ -11,6 +11,7 @@
 
 #include "alto_internal.cuh"
 #include "cpals.cuh"
+#include "handle.cuh"
 #include "encode.cuh"
 #include "mttkrp.cuh"
 
@@ -26,12 +27,9 @@ namespace {
 
 thread_local std::string g_last_error;
 
-struct ProfEvt {
-  int kind;
-  cudaEvent_t a, b;
-};
+}  // namespace
 
-alto_status fail(alto_status st, const char *fmt, ...) {
+alto_status alto::fail(alto_status st, const char *fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -41,80 +39,6 @@ alto_status fail(alto_status st, const char *fmt, ...) {
   return st;
 }
 
-#define CUDA_TRY(expr)                                                                       \
-  do {                                                                                       \
-    cudaError_t e_ = (expr);                                                                 \
-    if (e_ != cudaSuccess) return fail(ALTO_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
-  } while (0)
-
-struct PullPlan {
-  bool valid = false;
-  uint64_t *part_off = nullptr;  // [L]
-  uint64_t *row_ptr = nullptr;   // [I+1]
-  uint64_t *prow = nullptr;      // [entries]
-  uint64_t total_rows = 0;
-  uint64_t entries = 0;
-};
-
-struct HotTable {
-  int nslots = -1;
-  int hbits = 0;
-  uint64_t *htab = nullptr;
-};
-
-struct Buf {
-  void *p = nullptr;
-  size_t bytes = 0;
-};
-
-}  // namespace
-
-struct alto_tensor {
-  int N = 0, nbits = 0, kw = 1;
-  uint64_t M = 0;
-  uint64_t dims[kMaxModes] = {};
-  int bits[kMaxModes] = {};
-  uint64_t mask_lo[kMaxModes] = {}, mask_hi[kMaxModes] = {};
-  DecodePlan dp{};
-  DecodePlan32 dp32{};
-  BlockPlan bp{};
-  int rank_of[kMaxModes] = {};   // rank (order by length) of each mode
-  int mode_of[kMaxModes] = {};   // mode of each rank
-  alto_allocator alloc{};
-  bool user_alloc = false;
-  cudaStream_t stream = nullptr;
-  int device = 0, num_sms = 1;
-  size_t bytes_held = 0;
-  // device state
-  uint64_t *keys = nullptr;
-  float *vals = nullptr;
-  uint64_t *dims_dev = nullptr;
-  uint64_t L = 0;
-  uint32_t *intervals = nullptr;
-  uint32_t *max_len_dev = nullptr;
-  uint32_t *status_dev = nullptr;
-  double *norm_sq_dev = nullptr;
-  uint32_t *hot_rows[kMaxModes] = {};
-  uint32_t *nhot_dev = nullptr;
-  // host mirrors
-  uint32_t max_interval[kMaxModes] = {};
-  uint32_t nhot[kMaxModes] = {};
-  std::vector<uint32_t> hot_host[kMaxModes];
-  double norm_sq = 0.0;
-  std::vector<uint32_t> intervals_host;
-  bool intervals_host_valid = false;
-  // plans and caches
-  alto_mode_plan plan[kMaxModes];
-  HotTable hot_tab[kMaxModes];
-  PullPlan pull[kMaxModes];
-  Buf partials;
-  // instrumentation
-  bool prof_on = false;
-  std::vector<ProfEvt> prof_pending;
-  std::vector<cudaEvent_t> prof_pool;
-  double prof_ms[ALTO_PROF_KINDS] = {};
-  uint64_t prof_n[ALTO_PROF_KINDS] = {};
-};
 
 namespace {
 

@@ -1,0 +1,101 @@
+// The encoded-tensor handle behind alto_handle_t and the pieces of the C ABI
+// layer that more than one translation unit needs.
+#pragma once
+
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "alto_internal.cuh"
+
+namespace alto {
+
+// Sets the calling thread's error message (alto_last_error) and returns st.
+alto_status fail(alto_status st, const char *fmt, ...);
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail(ALTO_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct ProfEvt {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct PullPlan {
+  bool valid = false;
+  uint64_t *part_off = nullptr;  // [L]
+  uint64_t *row_ptr = nullptr;   // [I+1]
+  uint64_t *prow = nullptr;      // [entries]
+  uint64_t total_rows = 0;
+  uint64_t entries = 0;
+};
+
+struct HotTable {
+  int nslots = -1;
+  int hbits = 0;
+  uint64_t *htab = nullptr;
+};
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace alto
+
+struct alto_tensor {
+  using DecodePlan = alto::DecodePlan;
+  using DecodePlan32 = alto::DecodePlan32;
+  using BlockPlan = alto::BlockPlan;
+  using HotTable = alto::HotTable;
+  using PullPlan = alto::PullPlan;
+  using Buf = alto::Buf;
+  using ProfEvt = alto::ProfEvt;
+  int N = 0, nbits = 0, kw = 1;
+  uint64_t M = 0;
+  uint64_t dims[alto::kMaxModes] = {};
+  int bits[alto::kMaxModes] = {};
+  uint64_t mask_lo[alto::kMaxModes] = {}, mask_hi[alto::kMaxModes] = {};
+  DecodePlan dp{};
+  DecodePlan32 dp32{};
+  BlockPlan bp{};
+  int rank_of[alto::kMaxModes] = {};   // rank (order by length) of each mode
+  int mode_of[alto::kMaxModes] = {};   // mode of each rank
+  alto_allocator alloc{};
+  bool user_alloc = false;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 1;
+  size_t bytes_held = 0;
+  // device state
+  uint64_t *keys = nullptr;
+  float *vals = nullptr;
+  uint64_t *dims_dev = nullptr;
+  uint64_t L = 0;
+  uint32_t *intervals = nullptr;
+  uint32_t *max_len_dev = nullptr;
+  uint32_t *status_dev = nullptr;
+  double *norm_sq_dev = nullptr;
+  uint32_t *hot_rows[alto::kMaxModes] = {};
+  uint32_t *nhot_dev = nullptr;
+  // host mirrors
+  uint32_t max_interval[alto::kMaxModes] = {};
+  uint32_t nhot[alto::kMaxModes] = {};
+  std::vector<uint32_t> hot_host[alto::kMaxModes];
+  double norm_sq = 0.0;
+  std::vector<uint32_t> intervals_host;
+  bool intervals_host_valid = false;
+  // plans and caches
+  alto_mode_plan plan[alto::kMaxModes];
+  HotTable hot_tab[alto::kMaxModes];
+  PullPlan pull[alto::kMaxModes];
+  Buf partials;
+  // instrumentation
+  bool prof_on = false;
+  std::vector<ProfEvt> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[ALTO_PROF_KINDS] = {};
+  uint64_t prof_n[ALTO_PROF_KINDS] = {};
+};
