@@ -154,7 +154,7 @@ def traffic_from_profiles(kernel_src_sha):
 
 def kernel_src_sha():
     h = hashlib.sha256()
-    for f in ("mttkrp.cu", "mttkrp.cuh", "alto_internal.cuh"):
+    for f in ("mttkrp.cu", "mttkrp.cuh", "mttkrp_kernel.cuh", "alto_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2403_06348_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

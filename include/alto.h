@@ -102,9 +102,11 @@ typedef struct alto_info {
 /* Per-mode MTTKRP plan (what the autotuner sets). */
 typedef struct alto_mode_plan {
   int variant;        /* alto_variant                                             */
-  int cols_per_lane;  /* 4, 8 or 16 factor columns per thread: R/cols_per_lane
-                         threads work on one nonzero ("threads per nonzero");
-                         0 = library default                                    */
+  int cols_per_lane;  /* factor columns per thread: 4, 8 or 16 (< R) split one
+                         nonzero over R/cols_per_lane threads ("threads per
+                         nonzero"); cols_per_lane == R (R >= 8) gives each
+                         nonzero one thread, which walks its rows in 8-column
+                         chunks; 0 = library default                            */
   int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit             */
 } alto_mode_plan;
 

@@ -389,8 +389,13 @@ int hot_slots_that_fit(int R, int want) {
 
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   alto_mode_plan p = h->plan[mode];
-  if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16) p.cols_per_lane = 4;
+  if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16 &&
+      p.cols_per_lane != 32 && p.cols_per_lane != 64)
+    p.cols_per_lane = 4;
   while (R % p.cols_per_lane) p.cols_per_lane /= 2;
+  // one thread per nonzero needs R >= 8 (8-column chunks)
+  if (p.cols_per_lane == R && R < 8) p.cols_per_lane = 4;
+  if (p.cols_per_lane > 16 && p.cols_per_lane != R) p.cols_per_lane = 16;
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
   const bool pull_fits = pull_smem <= stage_budget() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
@@ -436,6 +441,8 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     memcpy(a.dp.runs[q], h->dp32.runs[m], sizeof(a.dp.runs[q]));
     a.factors[q] = m == mode ? nullptr : factors[m];
   }
+  for (int q = 0, k = 0; q < h->N; ++q)
+    if (h->mode_of[q] != mode) a.fin[k++] = factors[h->mode_of[q]];
   a.keys = h->keys;
   a.vals = h->vals;
   a.nnz = h->M;
@@ -465,6 +472,9 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     a.partials = static_cast<float *>(h->partials.p);
     a.part_off = pp.part_off;
     const size_t smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
+    if (p.cols_per_lane == R)
+      for (int m = 0; m < h->N; ++m)
+        if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
     {
       ProfScope ps(h, ALTO_PROF_MTTKRP, s);
       CUDA_TRY(launch_mttkrp(a, p.cols_per_lane, bf16, true, smem, h->num_sms, s));
@@ -474,6 +484,11 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
       CUDA_TRY(launch_pull_reduce(a.partials, pp.row_ptr, pp.prow, I, R, out, h->num_sms, s));
     }
   } else {
+    if (p.cols_per_lane == R) {
+      // one thread per nonzero reads 32-byte chunks: factors need 32-byte alignment
+      for (int m = 0; m < h->N; ++m)
+        if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
+    }
     if ((st = ensure_hot_table(h, mode, p.hot_rows, s)) != ALTO_OK) return st;
     const HotTable &ht = h->hot_tab[mode];
     a.htab = ht.htab;
@@ -852,8 +867,8 @@ alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *
   if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_PULL)
     return fail(ALTO_ERR_INVALID_ARG, "unknown variant %d", plan->variant);
   if (plan->cols_per_lane != 0 && plan->cols_per_lane != 4 && plan->cols_per_lane != 8 &&
-      plan->cols_per_lane != 16)
-    return fail(ALTO_ERR_INVALID_ARG, "cols_per_lane must be 0, 4, 8 or 16");
+      plan->cols_per_lane != 16 && plan->cols_per_lane != 32 && plan->cols_per_lane != 64)
+    return fail(ALTO_ERR_INVALID_ARG, "cols_per_lane must be 0, 4, 8, 16, 32 or 64");
   h->plan[mode] = *plan;
   return ALTO_OK;
 }

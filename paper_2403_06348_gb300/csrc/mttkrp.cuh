@@ -25,6 +25,7 @@ struct MttkrpArgs {
   uint64_t L;                  // line segments
   const uint32_t *intervals;   // [L][N][2] (original mode order)
   const void *factors[kMaxModes];  // by rank; the output rank's entry is unused
+  const void *fin[kMaxModes];      // the N-1 input factors, ranks in order without the output
   float *out;                  // [I_mode][R]
   int mode;                    // output mode in the original order
   int out_rank;                // its rank

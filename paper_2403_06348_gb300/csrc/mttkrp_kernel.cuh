@@ -154,6 +154,81 @@ __device__ __forceinline__ void decode_blocks(const BlockPlan &bp, uint64_t lo, 
   if constexpr (Q + 1 < N) decode_blocks<KW, N, Q + 1>(bp, lo, hi, c);
 }
 
+#ifndef ALTO_MTTKRP_RUNS
+#define ALTO_MTTKRP_RUNS 1
+#endif
+
+// The rounds of one batch: round q gives group grp the batch's nonzero
+// j = grp * tpn + q; the group gathers its N-1 input rows (lane `sub` holds the
+// column vectors sub, sub + tpn, ...), multiplies, and sums runs of equal
+// output row in registers before flushing them. TAIL batches check j < nvalid.
+template <int NMAX, int CPL, bool BF16, bool TAIL>
+__device__ __forceinline__ void group_rounds(const MttkrpArgs &a, int N, int tpn, int grp, int sub,
+                                             float v, int slot, uint32_t row,
+                                             const uint32_t (&in)[NMAX > 1 ? NMAX - 1 : 1], int nvalid,
+                                             float *temp, uint32_t rowb, uint32_t inb) {
+  constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
+  const unsigned full = 0xffffffffu;
+  const int R = a.R;
+  float run[CPL];
+#pragma unroll
+  for (int k = 0; k < CPL; ++k) run[k] = 0.f;
+  uint32_t run_row = kEmptyRow;
+  int run_slot = -1;
+#pragma unroll(CPL <= 8 ? 2 : 1)
+  for (int q = 0; q < tpn; ++q) {
+    const int j = grp * tpn + q;
+    const float vj = __shfl_sync(full, v, j);
+    const int sj = __shfl_sync(full, slot, j);
+    const uint32_t rj = __shfl_sync(full, row, j);
+    uint32_t ij[NIN];
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) ij[k] = (k + 1 < N) ? __shfl_sync(full, in[k], j) : 0u;
+    if (TAIL && j >= nvalid) continue;
+    float p[CPL];
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) {
+      if (k + 1 < N) {
+        const char *rb = static_cast<const char *>(a.fin[k]) + (uint64_t)ij[k] * rowb + inb;
+        float f[CPL];
+#pragma unroll
+        for (int w = 0; w < CPL / 4; ++w) {
+          const int voff = w * tpn * (BF16 ? 8 : 16);
+          if constexpr (!BF16) {
+            const float4 qv = __ldg(reinterpret_cast<const float4 *>(rb + voff));
+            f[4 * w] = qv.x;
+            f[4 * w + 1] = qv.y;
+            f[4 * w + 2] = qv.z;
+            f[4 * w + 3] = qv.w;
+          } else {
+            const uint2 qv = __ldg(reinterpret_cast<const uint2 *>(rb + voff));
+            f[4 * w] = bf16lo(qv.x);
+            f[4 * w + 1] = bf16hi(qv.x);
+            f[4 * w + 2] = bf16lo(qv.y);
+            f[4 * w + 3] = bf16hi(qv.y);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) p[c] = (k == 0 ? vj : p[c]) * f[c];
+      } else if (k == 0) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) p[c] = vj;
+      }
+    }
+    if (ALTO_MTTKRP_RUNS && rj == run_row) {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) run[c] += p[c];
+    } else {
+      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, a.out, R, sub, tpn);
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) run[c] = p[c];
+      run_row = rj;
+      run_slot = sj;
+    }
+  }
+  if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, a.out, R, sub, tpn);
+}
+
 template <int NT, int KW, int CPL, bool BF16, bool PULL>
 __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
   constexpr int NMAX = NT ? NT : kMaxModes;
@@ -164,8 +239,10 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
   const int tpn = R / CPL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int grp = lane / tpn, sub = lane - grp * tpn;
-  const unsigned full = 0xffffffffu;
   const int ro = a.out_rank;
+  // byte offset of this lane's first column vector, and the row strides
+  const uint32_t rowb = (uint32_t)R * (BF16 ? 2u : 4u);
+  const uint32_t inb = 4u * (uint32_t)sub * (BF16 ? 2u : 4u);
 
   uint64_t *htab = nullptr;
   if (!PULL) {
@@ -215,54 +292,24 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
         decode_blocks<KW, NMAX, 0>(a.bp, lo, hi, c);
       else
         decode_runs<KW, NMAX>(a.dp, N, lo, hi, c);
-      uint32_t row = 0;
+      // the output row and the N-1 input coordinates in a fixed order
+      constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
+      uint32_t row = c[0];
+      uint32_t in[NIN];
 #pragma unroll
-      for (int n = 0; n < NMAX; ++n)
+      for (int n = 1; n < NMAX; ++n)
         if (n == ro) row = c[n];
+#pragma unroll
+      for (int k = 0; k < NIN; ++k) in[k] = (NMAX > 1 && k + 1 < NMAX) ? (k < ro ? c[k] : c[k + 1]) : 0u;
       int slot = -1;
       if (valid) slot = PULL ? (int)(row - Ts) : hot_lookup(htab, a.hbits, row);
       const uint64_t rem = s1 - base;
-      const int nvalid = rem < 32 ? (int)rem : 32;
-
-      float run[CPL];
-#pragma unroll
-      for (int k = 0; k < CPL; ++k) run[k] = 0.f;
-      uint32_t run_row = kEmptyRow;
-      int run_slot = -1;
-      for (int q = 0; q < tpn; ++q) {
-        const int j = grp * tpn + q;
-        const float vj = __shfl_sync(full, v, j);
-        const int sj = __shfl_sync(full, slot, j);
-        const uint32_t rj = __shfl_sync(full, row, j);
-        uint32_t cj[NMAX];
-#pragma unroll
-        for (int n = 0; n < NMAX; ++n) cj[n] = (n < N && n != ro) ? __shfl_sync(full, c[n], j) : 0u;
-        if (j < nvalid) {
-          float p[CPL];
-#pragma unroll
-          for (int k = 0; k < CPL; ++k) p[k] = vj;
-#pragma unroll
-          for (int m = 0; m < NMAX; ++m) {
-            if (m < N && m != ro) {
-              float f[CPL];
-              load_row<CPL, BF16>(a.factors[m], cj[m], R, sub, tpn, f);
-#pragma unroll
-              for (int k = 0; k < CPL; ++k) p[k] *= f[k];
-            }
-          }
-          if (rj == run_row) {
-#pragma unroll
-            for (int k = 0; k < CPL; ++k) run[k] += p[k];
-          } else {
-            if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, a.out, R, sub, tpn);
-#pragma unroll
-            for (int k = 0; k < CPL; ++k) run[k] = p[k];
-            run_row = rj;
-            run_slot = sj;
-          }
-        }
-      }
-      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, a.out, R, sub, tpn);
+      if (rem >= 32)
+        group_rounds<NMAX, CPL, BF16, false>(a, N, tpn, grp, sub, v, slot, row, in, 32, temp, rowb,
+                                             inb);
+      else
+        group_rounds<NMAX, CPL, BF16, true>(a, N, tpn, grp, sub, v, slot, row, in, (int)rem, temp,
+                                            rowb, inb);
     }
     if (PULL) {
       __syncthreads();
@@ -293,6 +340,169 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
       __syncthreads();
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// One thread per nonzero ("threads per nonzero" = 1). A thread decodes its
+// nonzero, then walks the row in chunks of 8 columns: one 32-byte load per
+// input factor row (a whole sector), 8 products per input mode, and the chunk
+// leaves through two 16-byte vector atomics (cold row) or 8 shared-memory
+// atomics (hot row / Temp). No shuffles; each warp keeps 32 independent row
+// gathers in flight. The staging table here swizzles every column by the low
+// bits of its slot, so threads on different rows use different banks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int lpn_swizzle(int slot, int R) { return slot & ((R < 32 ? R : 32) - 1); }
+
+template <bool BF16>
+__device__ __forceinline__ void load8(const void *base, uint64_t off, float (&f)[8]) {
+  if constexpr (!BF16) {
+    const float *p = static_cast<const float *>(base) + off;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]), "=f"(f[7])
+        : "l"(p));
+  } else {
+    const uint4 q = __ldg(reinterpret_cast<const uint4 *>(static_cast<const __nv_bfloat16 *>(base) + off));
+    f[0] = bf16lo(q.x);
+    f[1] = bf16hi(q.x);
+    f[2] = bf16lo(q.y);
+    f[3] = bf16hi(q.y);
+    f[4] = bf16lo(q.z);
+    f[5] = bf16hi(q.z);
+    f[6] = bf16lo(q.w);
+    f[7] = bf16hi(q.w);
+  }
+}
+
+template <int NT, int KW, bool BF16, bool PULL>
+__global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm)
+    mttkrp_lpn_kernel(const __grid_constant__ MttkrpArgs a) {
+  constexpr int NMAX = NT ? NT : kMaxModes;
+  const int N = NT ? NT : a.dp.nmodes;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float *temp = reinterpret_cast<float *>(sm);
+  const int R = a.R;
+  const int ro = a.out_rank;
+
+  uint64_t *htab = nullptr;
+  if (!PULL) {
+    htab = reinterpret_cast<uint64_t *>(temp + (size_t)a.nslots * R);
+    const int hsize = 1 << a.hbits;
+    for (int i = threadIdx.x; i < hsize; i += blockDim.x) htab[i] = a.htab[i];
+    for (int i = threadIdx.x; i < a.nslots * R; i += blockDim.x) temp[i] = 0.f;
+    __syncthreads();
+  }
+
+  int since_flush = 0;
+  for (uint64_t l = blockIdx.x; l < a.L; l += gridDim.x) {
+    const uint64_t s0 = (l * a.nnz) / a.L, s1 = ((l + 1) * a.nnz) / a.L;
+    uint32_t Ts = 0, len = 0;
+    if (PULL) {
+      if (s1 > s0) {
+        Ts = a.intervals[(l * (uint64_t)N + a.mode) * 2];
+        len = a.intervals[(l * (uint64_t)N + a.mode) * 2 + 1] - Ts + 1u;
+      }
+      for (uint32_t i = threadIdx.x; i < len * (uint32_t)R; i += blockDim.x) temp[i] = 0.f;
+      __syncthreads();
+    }
+    for (uint64_t x = s0 + threadIdx.x; x < s1; x += blockDim.x) {
+      uint64_t lo, hi = 0;
+      if (KW == 1) {
+        lo = __ldcs(reinterpret_cast<const unsigned long long *>(a.keys) + x);
+      } else {
+        const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2 *>(a.keys) + x);
+        lo = kk.x;
+        hi = kk.y;
+      }
+      const float v = __ldcs(a.vals + x);
+      uint32_t c[NMAX];
+      if constexpr (NT > 0)
+        decode_blocks<KW, NMAX, 0>(a.bp, lo, hi, c);
+      else
+        decode_runs<KW, NMAX>(a.dp, N, lo, hi, c);
+      uint32_t row = 0;
+#pragma unroll
+      for (int n = 0; n < NMAX; ++n)
+        if (n == ro) row = c[n];
+      const int slot = PULL ? (int)(row - Ts) : hot_lookup(htab, a.hbits, row);
+      const int sw = slot >= 0 ? lpn_swizzle(slot, R) : 0;
+      float *trow = temp + (size_t)(slot >= 0 ? slot : 0) * R;
+      float *orow = a.out + (uint64_t)row * (uint64_t)R;
+      for (int cc = 0; cc < R; cc += 8) {
+        float p[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[k] = v;
+#pragma unroll
+        for (int m = 0; m < NMAX; ++m) {
+          if (m < N && m != ro) {
+            float f[8];
+            load8<BF16>(a.factors[m], (uint64_t)c[m] * (uint64_t)R + cc, f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) p[k] *= f[k];
+          }
+        }
+        if (slot >= 0) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) atomicAdd(trow + ((cc + k) ^ sw), p[k]);
+        } else {
+          red_v4(orow + cc, p[0], p[1], p[2], p[3]);
+          red_v4(orow + cc + 4, p[4], p[5], p[6], p[7]);
+        }
+      }
+    }
+    if (PULL) {
+      __syncthreads();
+      if (len) {
+        float *dst = a.partials + a.part_off[l] * (uint64_t)R;
+        const uint32_t n = len * (uint32_t)R;
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+          const uint32_t r = i / (uint32_t)R, col = i - r * (uint32_t)R;
+          dst[i] = temp[r * R + (col ^ lpn_swizzle((int)r, R))];
+        }
+      }
+      __syncthreads();
+    } else if (++since_flush >= a.flush_every || l + gridDim.x >= a.L) {
+      since_flush = 0;
+      __syncthreads();
+      const int n = a.nslots * R;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float t = temp[i];
+        if (t != 0.f) {
+          const int sl = i / R, col = (i - sl * R) ^ lpn_swizzle(sl, R);
+          atomicAdd(a.out + (uint64_t)a.slot_rows[sl] * (uint64_t)R + col, t);
+          temp[i] = 0.f;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <int NT, int KW, bool BF16, bool PULL>
+static cudaError_t launch_lpn(const MttkrpArgs &a, size_t smem, int num_sms, cudaStream_t s) {
+  auto kern = mttkrp_lpn_kernel<NT, KW, BF16, PULL>;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mttkrp_smem_limit());
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  uint64_t grid = (uint64_t)num_sms * kMttkrpBlocksPerSm;
+  if (grid > a.L) grid = a.L;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, kMttkrpThreads, smem, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <int NT, int KW>
+static cudaError_t launch_lpn_k(const MttkrpArgs &a, bool bf16, bool pull, size_t smem, int num_sms,
+                                cudaStream_t s) {
+  if (bf16)
+    return pull ? launch_lpn<NT, KW, true, true>(a, smem, num_sms, s)
+                : launch_lpn<NT, KW, true, false>(a, smem, num_sms, s);
+  return pull ? launch_lpn<NT, KW, false, true>(a, smem, num_sms, s)
+              : launch_lpn<NT, KW, false, false>(a, smem, num_sms, s);
 }
 
 template <int NT, int KW, int CPL, bool BF16, bool PULL>
@@ -326,6 +536,9 @@ static cudaError_t launch_kc(const MttkrpArgs &a, bool bf16, bool pull, size_t s
 template <int NT>
 cudaError_t launch_mttkrp_nt(const MttkrpArgs &a, int cpl, bool bf16, bool pull, size_t smem,
                              int num_sms, cudaStream_t s) {
+  if (cpl == a.R && a.R >= 8)
+    return a.dp.kw == 1 ? launch_lpn_k<NT, 1>(a, bf16, pull, smem, num_sms, s)
+                        : launch_lpn_k<NT, 2>(a, bf16, pull, smem, num_sms, s);
   if (a.dp.kw == 1) {
     if (cpl == 4) return launch_kc<NT, 1, 4>(a, bf16, pull, smem, num_sms, s);
     if (cpl == 8) return launch_kc<NT, 1, 8>(a, bf16, pull, smem, num_sms, s);

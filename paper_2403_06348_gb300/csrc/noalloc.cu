@@ -100,6 +100,8 @@ extern "C" alto_status alto_mttkrp_noalloc(alto_handle_t h, int mode, const void
     memcpy(a.dp.runs[q], h->dp32.runs[m], sizeof(a.dp.runs[q]));
     a.factors[q] = m == mode ? nullptr : factors[m];
   }
+  for (int q = 0, k = 0; q < h->N; ++q)
+    if (h->mode_of[q] != mode) a.fin[k++] = factors[h->mode_of[q]];
   a.keys = h->keys;
   a.vals = h->vals;
   a.nnz = h->M;

@@ -44,8 +44,10 @@ def _run_modes(coords, vals, dims, R, variant=0, cpl=0, bf16=False, seed=0, mode
     return t, worst
 
 
+# cols_per_lane: 4 and 8 split a nonzero over R/4 or R/8 lanes; 16 (= R here)
+# is the one-thread-per-nonzero kernel
 @pytest.mark.parametrize("variant", [0, 1, 2])
-@pytest.mark.parametrize("cpl", [4, 8])
+@pytest.mark.parametrize("cpl", [4, 8, 16])
 def test_uniform_3d_all_modes(variant, cpl):
     spec = synth.CONFIGS[0]
     coords, vals = synth.generate(spec)
@@ -53,30 +55,41 @@ def test_uniform_3d_all_modes(variant, cpl):
 
 
 @pytest.mark.parametrize("R", [4, 8, 16, 32, 64])
-def test_ranks(R):
+@pytest.mark.parametrize("one_thread", [False, True])
+def test_ranks(R, one_thread):
     coords, vals = gu.rand_tensor((300, 200, 150), 40_000, 3)
-    _run_modes(coords, vals, (300, 200, 150), R, seed=R)
+    _run_modes(coords, vals, (300, 200, 150), R, seed=R, cpl=R if one_thread else 0)
 
 
 @pytest.mark.parametrize("variant", [1, 2])
-def test_bf16_factors(variant):
+@pytest.mark.parametrize("cpl", [4, 16])
+def test_bf16_factors(variant, cpl):
     spec = synth.CONFIGS[0]
     coords, vals = synth.generate(spec)
-    _run_modes(coords, vals, spec.dims, 16, variant=variant, bf16=True, seed=2)
+    _run_modes(coords, vals, spec.dims, 16, variant=variant, cpl=cpl, bf16=True, seed=2)
 
 
-def test_five_modes_two_word_positions():
+@pytest.mark.parametrize("cpl", [4, 64])
+def test_five_modes_two_word_positions(cpl):
     spec = synth.scaled(synth.CONFIGS[3], 300_000)
     coords, vals = synth.generate(spec)
-    _run_modes(coords, vals, spec.dims, 64, seed=4)
-    _run_modes(coords, vals, spec.dims, 64, bf16=True, seed=4)
+    _run_modes(coords, vals, spec.dims, 64, cpl=cpl, seed=4)
+    _run_modes(coords, vals, spec.dims, 64, cpl=cpl, bf16=True, seed=4)
 
 
-def test_zipf_hot_rows():
+@pytest.mark.parametrize("cpl", [4, 8, 32])
+def test_zipf_hot_rows(cpl):
     spec = synth.scaled(synth.CONFIGS[1], 2_000_000)
     coords, vals = synth.generate(spec)
-    _run_modes(coords, vals, spec.dims, 32, variant=1, seed=5)
-    _run_modes(coords, vals, spec.dims, 32, variant=1, seed=5, cpl=4)
+    _run_modes(coords, vals, spec.dims, 32, variant=1, seed=5, cpl=cpl)
+
+
+def test_six_and_two_modes_generic_kernel():
+    """N outside {3, 4, 5} runs the kernel with a run-time number of modes."""
+    for dims in [(40, 30, 20, 10, 8, 6), (500, 300)]:
+        coords, vals = gu.rand_tensor(dims, 30_000, len(dims))
+        _run_modes(coords, vals, dims, 16, seed=7)
+        _run_modes(coords, vals, dims, 16, seed=7, cpl=16)
 
 
 def test_count_tensor_small_modes_pull():
@@ -85,6 +98,7 @@ def test_count_tensor_small_modes_pull():
     t, _ = _run_modes(coords, vals, spec.dims, 16, seed=6)
     assert t.get_mode_plan(3, 16)[0] == 2   # 24 rows, reuse 83k: pull
     _run_modes(coords, vals, spec.dims, 16, variant=2, seed=6, modes=[2, 3])
+    _run_modes(coords, vals, spec.dims, 16, variant=2, seed=6, modes=[2, 3], cpl=16)
     _run_modes(coords, vals, spec.dims, 16, variant=1, seed=6, modes=[2, 3])
 
 
