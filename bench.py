@@ -47,6 +47,9 @@ def parse_args():
     p.add_argument("--nnz", type=int, default=0, help="override nonzeros (testing only)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the served CP-ALS workload")
+    p.add_argument("--serve-requests", type=int, default=2000)
+    p.add_argument("--serve-pool", type=int, default=64)
     return p.parse_args()
 
 
@@ -347,6 +350,8 @@ def run_ours(args):
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, alto, coords, vals, spec, A0, world, barrier)
+    if not args.no_serve:
+        line["serving"] = run_serving(args, alto)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         sample = min(M, 2_000_000)
@@ -362,6 +367,72 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _gen_request(r):
+    import synth
+    return synth.request_tensor(r)
+
+
+def run_serving(args, alto):
+    """Served CP-ALS: Poisson arrivals (200 requests/s) of CP-ALS requests
+    (20 iterations; 3-5 modes, dims log-uniform 100..1M, nnz log-uniform
+    1e3..1e7, Zipf(1.1) coordinates, values U(0,1], R in {8,16,32}), through
+    the continuous-batching Server and, on the same schedule, one request at a
+    time (FCFS, cpals_run). Requests carry host COO data; factors are drawn on
+    the GPU from the request's seed and come back to pinned host memory.
+    Latency = results on the host - arrival."""
+    import concurrent.futures
+    import multiprocessing
+    import threading
+    import synth
+    from paper_2403_06348_gb300 import serve
+
+    pool, reqs = synth.request_pool_stream(count=args.serve_requests, pool=args.serve_pool)
+    t0 = time.perf_counter()
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                                mp_context=ctx) as ex:
+        tensors = list(ex.map(_gen_request, pool))
+    gen_s = time.perf_counter() - t0
+    items = [(r.arrival_s, tensors[r.rid][0], tensors[r.rid][1], r.dims, r.rank, r.iters, None,
+              r.seed % (1 << 27)) for r in reqs]
+    # warm-up: one small request through each arm
+    small = min(range(len(pool)), key=lambda j: pool[j].nnz)
+    w = (0.0, tensors[small][0], tensors[small][1], pool[small].dims, 8, 2, None, 1)
+    srv = serve.Server(budget_bytes=100e9)
+    srv.submit(w[1], w[2], w[3], w[4], w[5], seed=w[7]).result(timeout=120)
+    srv.close()
+    serve.run_fcfs([w], time.perf_counter())
+
+    srv = serve.Server(budget_bytes=100e9)
+    start = time.perf_counter() + 0.05
+    futs = []
+
+    def producer():
+        for it in items:
+            at = start + it[0]
+            now = time.perf_counter()
+            if now < at:
+                time.sleep(at - now)
+            futs.append(srv.submit(it[1], it[2], it[3], it[4], it[5], seed=it[7], arrival=at))
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    results = [f.result(timeout=3600) for f in futs]
+    srv.close()
+    served = srv.stats()
+    fcfs = serve.run_fcfs(items, time.perf_counter() + 0.05)
+    nnz = [len(it[2]) for it in items]
+    return {"workload": (f"{len(items)} CP-ALS requests (20 iters), Poisson 200/s, 3-5 modes, dims "
+                         f"log-U[100,1M], nnz log-U[1e3,1e7] (pool of {len(pool)} tensors, "
+                         f"mean nnz {np.mean(nnz):.3g}), Zipf 1.1, R in {{8,16,32}}, 100 GB budget"),
+            "served": served, "one_at_a_time": fcfs,
+            "throughput_ratio": served["nnz_r_iters_per_s"] / fcfs["nnz_r_iters_per_s"],
+            "p99_ratio": fcfs["p99_s"] / served["p99_s"],
+            "not_spd": sum(1 for r in results if r.status != 0),
+            "generate_s": gen_s}
 
 
 def run_e2e(args, alto, coords, vals, spec, A0, world, barrier):

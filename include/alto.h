@@ -228,6 +228,72 @@ alto_status alto_mttkrp_noalloc(alto_handle_t h, int mode, const void *const *fa
                                 alto_dtype fdtype, int R, float *out, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * alto_mttkrp_grouped -- n MTTKRPs (Alg. 3 and 4) over n encoded tensors in
+ * one persistent kernel launch. The tensors may differ in nnz, number of
+ * modes, key width and rank.
+ *
+ * The units of work are the line segments of every handle (Section IV-A);
+ * the GPU's CTAs take them in turn, so many small tensors share the device
+ * without a launch each. Per segment, the output rows of the segment's mode
+ * interval are staged in shared memory when they fit (interval x R x 4 bytes
+ * <= about 220 KB) and flushed once with vector atomics; otherwise equal-row
+ * runs go straight to the output with vector atomics. The hot-row tables and
+ * the PULL partials of alto_mttkrp are not used. Work is balanced by segment,
+ * so tensors whose segments hold very different numbers of nonzeros share it
+ * less evenly (alto_set_partitions sets a handle's segment count).
+ *
+ *  n        number of problems (0 does nothing).
+ *  hs       host [n] handles (a handle may appear more than once).
+ *  modes    host [n] output mode of each problem.
+ *  factors  host [n] arrays, each a host array [nmodes of that handle] of
+ *           device pointers to I_m x R row-major matrices, 16-byte aligned;
+ *           the output mode's entry is ignored.
+ *  Rs       host [n] ranks (4, 8, 16, 32 or 64).
+ *  fdtype   ALTO_F32 or ALTO_BF16, for every problem.
+ *  outs     host [n] device pointers to I_mode x R floats, 16-byte aligned,
+ *           overwritten (zeroed with cudaMemsetAsync, then accumulated).
+ *  stream   all handles must be ready on this stream.
+ * Allocates and frees (stream-ordered) one small table per call. Results are
+ * rounded like alto_mttkrp's: fp32 sums in an order that varies run to run.
+ * Errors: INVALID_ARG (which problem and why in alto_last_error), UNSUPPORTED,
+ * CUDA.
+ * ------------------------------------------------------------------------- */
+alto_status alto_mttkrp_grouped(int n, const alto_handle_t *hs, const int *modes,
+                                const void *const *const *factors, const int *Rs, alto_dtype fdtype,
+                                float *const *outs, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * alto_autotune -- picks, by measurement, each mode's MTTKRP plan (ATOMIC or
+ * PULL, 4 or 8 columns per lane; hot rows as the library sizes them) and,
+ * with ALTO_TUNE_SEGMENTS, the segment count among the current one and
+ * segments of 4 Ki, 16 Ki and 64 Ki nonzeros. The paper chooses between its
+ * two traversals by the per-mode fiber-reuse rule (Section IV-B); here that
+ * rule is only the default, and the choice is the fastest measured plan.
+ * Every candidate runs once untimed and twice timed (CUDA events, the faster
+ * counts); the sum over modes decides the segment count. The winners stay set
+ * on the handle (alto_get_mode_plan reads them).
+ *
+ *  factors  as in alto_mttkrp (all modes set; device, 16-byte aligned).
+ *  out      device scratch of max_n I_n x R floats (overwritten).
+ *  flags    0 or ALTO_TUNE_SEGMENTS.
+ *  res      the chosen plan (resolved), its time and the default plan's time
+ *           per mode, the segment count, and the number of timed candidates.
+ * Synchronises the stream. Errors: those of alto_mttkrp.
+ * ------------------------------------------------------------------------- */
+#define ALTO_TUNE_SEGMENTS 1
+
+typedef struct alto_tune_result {
+  alto_mode_plan plan[ALTO_MAX_MODES];
+  double ms[ALTO_MAX_MODES];          /* chosen plan, ms per MTTKRP          */
+  double default_ms[ALTO_MAX_MODES];  /* library default at the original L  */
+  uint64_t nparts;
+  int candidates;
+} alto_tune_result;
+
+alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, alto_dtype fdtype,
+                          float *out, int flags, void *stream, alto_tune_result *res);
+
+/* ---------------------------------------------------------------------------
  * cpals_run -- CP-ALS, Alg. 1: for each iteration and each mode n:
  * V = Hadamard product of the Grams G_m = A^(m)T A^(m), m != n (fp64);
  * M = MTTKRP (alto_mttkrp); A^(n) = M V^-1 through a Cholesky factorisation of
@@ -252,6 +318,83 @@ alto_status alto_mttkrp_noalloc(alto_handle_t h, int mode, const void *const *fa
  * ------------------------------------------------------------------------- */
 alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, double *lambda,
                       double *fits, double tol, int *iters_done, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * CP-ALS batch -- many CP-ALS runs (Alg. 1) on different tensors advanced
+ * together on one stream: a step performs one mode update of every active run
+ * (prepare, grouped MTTKRP, update, finish: the same arithmetic as cpals_run),
+ * replayed from one CUDA graph. Runs join and leave between steps; each run
+ * keeps its own iteration, mode and stop rule on the device. No counterpart in
+ * the paper: it batches the paper's per-tensor loop.
+ *
+ * alto_batch_create  max_slots 1..4096 concurrent runs; alloc as in
+ *                    alto_encode (NULL = cudaMallocAsync); stream NULL = a new
+ *                    non-blocking stream owned by the batch. Every call below
+ *                    is ordered on that stream.
+ * alto_batch_add     admits a run of CP-ALS on handle h: rank R, at most iters
+ *                    iterations, tol as in cpals_run, initial factors
+ *                    (host array [nmodes] of host or device pointers, copied
+ *                    in). The batch orders itself after the handle's stream,
+ *                    may re-partition the handle into segments of about 4096
+ *                    nonzeros, and reads h until alto_batch_remove. *slot
+ *                    receives the run's slot. Errors: INVALID_ARG,
+ *                    UNSUPPORTED (rank, no free slot), OOM, CUDA.
+ * alto_batch_step    enqueues nsteps steps and one asynchronous read-back of
+ *                    the runs' states; returns without waiting (it waits only
+ *                    when four read-backs are still outstanding).
+ * alto_batch_poll    writes up to cap slots whose runs have ended, as seen by
+ *                    the completed read-backs, to slots[]; wait != 0 waits for
+ *                    the oldest outstanding read-back when none has ended yet.
+ * alto_batch_result  for a slot reported by alto_batch_poll: enqueues the
+ *                    normalised factors (A_m = B_m diag(s_m)) into factors[m]
+ *                    (host or device; NULL entries skipped), lambda [R] and
+ *                    fits [iters] (host or device, nullable) on the batch
+ *                    stream; host destinations are valid after
+ *                    alto_batch_sync (pin them for asynchronous copies).
+ *                    *iters_done and *run_status (ALTO_OK or
+ *                    ALTO_ERR_NOT_SPD) come from the read-back.
+ * alto_batch_remove  frees the slot (stream-ordered) and orders the handle's
+ *                    stream after the batch, so the handle may then be freed.
+ * alto_batch_sync    waits for everything enqueued on the batch stream.
+ * alto_cpals_footprint  device bytes one run holds while resident (encoded
+ *                    tensor + CP-ALS state) and at its peak (plus the encode's
+ *                    transient buffers), for admission by memory budget.
+ * ------------------------------------------------------------------------- */
+typedef struct alto_batch *alto_batch_t;
+
+typedef struct alto_batch_info {
+  int active;                /* runs admitted and not removed                   */
+  int slots_span;            /* highest slot in use + 1 (as of the last step)   */
+  uint64_t steps;            /* steps enqueued                                   */
+  uint64_t graph_launches;   /* graph launches enqueued                          */
+  uint64_t bytes_held;       /* device bytes held by the batch                   */
+  int pending_readbacks;
+} alto_batch_info;
+
+alto_status alto_batch_create(int max_slots, const alto_allocator *alloc, void *stream,
+                              alto_batch_t *out);
+void alto_batch_free(alto_batch_t b);
+alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, double tol,
+                           const float *const *factors, int *slot);
+alto_status alto_batch_step(alto_batch_t b, int nsteps);
+alto_status alto_batch_poll(alto_batch_t b, int wait, int *slots, int cap, int *ndone);
+alto_status alto_batch_result(alto_batch_t b, int slot, float *const *factors, double *lambda,
+                              double *fits, int *iters_done, int *run_status);
+alto_status alto_batch_remove(alto_batch_t b, int slot);
+alto_status alto_batch_query(alto_batch_t b, alto_batch_info *info);
+alto_status alto_batch_sync(alto_batch_t b);
+alto_status alto_cpals_footprint(int nmodes, const uint64_t *dims, uint64_t nnz, int R, int iters,
+                                 uint64_t *resident, uint64_t *peak);
+
+/* ---------------------------------------------------------------------------
+ * alto_fill_uniform -- n floats of dst (device) set to seeded uniform values
+ * in [0, 1): element i is (SplitMix64(seed * 2^32 + i) >> 40) * 2^-24, where
+ * SplitMix64(x) = mix(x + 0x9E3779B97F4A7C15) with the published finaliser
+ * (Steele, Lea and Flood, 2014). For initial CP-ALS factors drawn on the GPU;
+ * the paper leaves the initialisation to the caller. seed < 2^32, n <= 2^32.
+ * Asynchronous on stream. Errors: INVALID_ARG, CUDA.
+ * ------------------------------------------------------------------------- */
+alto_status alto_fill_uniform(float *dst, uint64_t n, uint64_t seed, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to report kernel time

@@ -69,6 +69,21 @@ class alto_mode_plan(ctypes.Structure):
                 ("hot_rows", ctypes.c_int)]
 
 
+class alto_tune_result(ctypes.Structure):
+    _fields_ = [("plan", alto_mode_plan * ALTO_MAX_MODES), ("ms", ctypes.c_double * ALTO_MAX_MODES),
+                ("default_ms", ctypes.c_double * ALTO_MAX_MODES), ("nparts", ctypes.c_uint64),
+                ("candidates", ctypes.c_int)]
+
+
+ALTO_TUNE_SEGMENTS = 1
+
+
+class alto_batch_info(ctypes.Structure):
+    _fields_ = [("active", ctypes.c_int), ("slots_span", ctypes.c_int), ("steps", ctypes.c_uint64),
+                ("graph_launches", ctypes.c_uint64), ("bytes_held", ctypes.c_uint64),
+                ("pending_readbacks", ctypes.c_int)]
+
+
 # Exported symbols and their ctypes signatures (mirrors include/alto.h).
 _vp, _u64, _i32, _u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
 SIGNATURES = {
@@ -86,6 +101,21 @@ SIGNATURES = {
     "cpals_run": ([_vp, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_i32), _vp],
                   _i32),
     "alto_mttkrp_noalloc": ([_vp, _i32, _vp, _i32, _i32, _vp, _vp], _i32),
+    "alto_mttkrp_grouped": ([_i32, _vp, _vp, _vp, _vp, _i32, _vp, _vp], _i32),
+    "alto_batch_create": ([_i32, _vp, _vp, ctypes.POINTER(_vp)], _i32),
+    "alto_batch_free": ([_vp], None),
+    "alto_batch_add": ([_vp, _vp, _i32, _i32, ctypes.c_double, _vp, ctypes.POINTER(_i32)], _i32),
+    "alto_batch_step": ([_vp, _i32], _i32),
+    "alto_batch_poll": ([_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)], _i32),
+    "alto_batch_result": ([_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+                          _i32),
+    "alto_batch_remove": ([_vp, _i32], _i32),
+    "alto_batch_query": ([_vp, ctypes.POINTER(alto_batch_info)], _i32),
+    "alto_batch_sync": ([_vp], _i32),
+    "alto_cpals_footprint": ([_i32, _vp, _u64, _i32, _i32, ctypes.POINTER(_u64),
+                              ctypes.POINTER(_u64)], _i32),
+    "alto_fill_uniform": ([_vp, _u64, _u64, _vp], _i32),
+    "alto_autotune": ([_vp, _i32, _vp, _i32, _vp, _i32, _vp, ctypes.POINTER(alto_tune_result)], _i32),
     "alto_profile_enable": ([_vp, _i32], _i32),
     "alto_profile_read": ([_vp, ctypes.POINTER(alto_profile), _i32], _i32),
     "alto_kernel_launches": ([], _u64),
@@ -210,6 +240,107 @@ def cpals_run(t: "AltoTensor", R: int, iters: int, factors, lam, fits: Optional[
     return int(done.value)
 
 
+def alto_mttkrp_grouped(problems, dtype: int = ALTO_F32, stream=None) -> None:
+    """One grouped launch over ``problems``: a sequence of
+    (tensor, mode, factors, R, out) tuples (factors and out CUDA tensors)."""
+    n = len(problems)
+    if n == 0:
+        return
+    hs = (ctypes.c_void_p * n)(*[p[0].handle for p in problems])
+    modes = (ctypes.c_int * n)(*[int(p[1]) for p in problems])
+    fac_arrays = [(ctypes.c_void_p * p[0].nmodes)(*[_ptr(f) for f in p[2]]) for p in problems]
+    facs = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in fac_arrays])
+    Rs = (ctypes.c_int * n)(*[int(p[3]) for p in problems])
+    outs = (ctypes.c_void_p * n)(*[_ptr(p[4]) for p in problems])
+    _check(lib().alto_mttkrp_grouped(n, hs, modes, facs, Rs, int(dtype), outs,
+                                     _stream_ptr(stream)))
+
+
+def alto_fill_uniform(dst, seed: int, stream=None) -> None:
+    """Seeded uniform [0, 1) fill of a float32 CUDA tensor (see include/alto.h)."""
+    _check(lib().alto_fill_uniform(_ptr(dst), int(dst.numel()), int(seed), _stream_ptr(stream)))
+
+
+def alto_cpals_footprint(dims: Sequence[int], nnz: int, R: int, iters: int) -> Tuple[int, int]:
+    """(resident, peak) device bytes of one CP-ALS run in a batch."""
+    d = (ctypes.c_uint64 * len(dims))(*[int(x) for x in dims])
+    res, peak = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(lib().alto_cpals_footprint(len(dims), d, int(nnz), int(R), int(iters),
+                                      ctypes.byref(res), ctypes.byref(peak)))
+    return int(res.value), int(peak.value)
+
+
+class Batch:
+    """CP-ALS batch (alto_batch_*): runs on many tensors advanced together,
+    one mode update of every active run per step, replayed from a CUDA graph."""
+
+    def __init__(self, max_slots: int = 1024, stream=None):
+        torch = _torch()
+        self._b = None
+        # the batch runs on its own stream; inputs made on the caller's current
+        # stream are ordered before each add, and results after each result()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        b = ctypes.c_void_p()
+        _check(lib().alto_batch_create(int(max_slots), None, _stream_ptr(self.stream),
+                                       ctypes.byref(b)))
+        self._b = b
+        self._tensors = {}
+
+    def add(self, t: "AltoTensor", R: int, iters: int, factors, tol: float = 0.0) -> int:
+        torch = _torch()
+        self.stream.wait_stream(torch.cuda.current_stream())
+        arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
+        slot = ctypes.c_int(-1)
+        _check(lib().alto_batch_add(self._b, t.handle, int(R), int(iters), float(tol), arr,
+                                    ctypes.byref(slot)))
+        self._tensors[slot.value] = t
+        return int(slot.value)
+
+    def step(self, nsteps: int = 1) -> None:
+        _check(lib().alto_batch_step(self._b, int(nsteps)))
+
+    def poll(self, wait: bool = False, cap: int = 4096) -> List[int]:
+        buf = (ctypes.c_int * cap)()
+        n = ctypes.c_int(0)
+        _check(lib().alto_batch_poll(self._b, 1 if wait else 0, buf, cap, ctypes.byref(n)))
+        return [int(buf[i]) for i in range(n.value)]
+
+    def result(self, slot: int, factors, lam=None, fits=None) -> Tuple[int, int]:
+        """Enqueue the run's normalised factors (and lambda / fits) into the
+        given buffers; returns (iters_done, run_status)."""
+        t = self._tensors[slot]
+        arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
+        done, st = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().alto_batch_result(self._b, int(slot), arr, _ptr(lam) if lam is not None else None,
+                                       _ptr(fits) if fits is not None else None, ctypes.byref(done),
+                                       ctypes.byref(st)))
+        _torch().cuda.current_stream().wait_stream(self.stream)
+        return int(done.value), int(st.value)
+
+    def remove(self, slot: int) -> None:
+        _check(lib().alto_batch_remove(self._b, int(slot)))
+        self._tensors.pop(slot, None)
+
+    def sync(self) -> None:
+        _check(lib().alto_batch_sync(self._b))
+
+    def info(self) -> alto_batch_info:
+        i = alto_batch_info()
+        _check(lib().alto_batch_query(self._b, ctypes.byref(i)))
+        return i
+
+    def free(self) -> None:
+        if self._b:
+            lib().alto_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # handle wrapper
 # ---------------------------------------------------------------------------
@@ -310,6 +441,30 @@ class AltoTensor:
             out = torch.empty((rows, R), dtype=torch.float32, device="cuda")
         alto_mttkrp(self, mode, factors, R, out, code, stream)
         return out
+
+    def autotune(self, factors, R: int, out=None, segments: bool = True, dtype=None,
+                 stream=None) -> dict:
+        """alto_autotune: measured per-mode plan (and segment count); the
+        winners stay set on the handle. Returns the report as a dict."""
+        torch = _torch()
+        code = ALTO_F32
+        if dtype is not None:
+            code = dtype
+        elif any(f is not None and f.dtype == torch.bfloat16 for f in factors):
+            code = ALTO_BF16
+        if out is None:
+            out = torch.empty((max(self.dims), R), dtype=torch.float32, device="cuda")
+        arr = (ctypes.c_void_p * self.nmodes)(*[_ptr(f) for f in factors])
+        res = alto_tune_result()
+        _check(lib().alto_autotune(self.handle, int(R), arr, int(code), _ptr(out),
+                                   ALTO_TUNE_SEGMENTS if segments else 0, _stream_ptr(stream),
+                                   ctypes.byref(res)))
+        n = self.nmodes
+        return {"plans": [(int(res.plan[i].variant), int(res.plan[i].cols_per_lane),
+                           int(res.plan[i].hot_rows)) for i in range(n)],
+                "ms": [float(res.ms[i]) for i in range(n)],
+                "default_ms": [float(res.default_ms[i]) for i in range(n)],
+                "nparts": int(res.nparts), "candidates": int(res.candidates)}
 
     def cpals(self, R: int, iters: int, factors, tol: float = 0.0, stream=None):
         """Run CP-ALS in place on ``factors`` (CUDA float32 tensors or numpy

@@ -40,9 +40,7 @@ alto_status alto::fail(alto_status st, const char *fmt, ...) {
 }
 
 
-namespace {
-
-void *dalloc(alto_tensor *h, size_t bytes, cudaStream_t s) {
+void *alto::dalloc(alto_tensor *h, size_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 16;
   void *p = nullptr;
   if (h->user_alloc) {
@@ -55,7 +53,7 @@ void *dalloc(alto_tensor *h, size_t bytes, cudaStream_t s) {
   return p;
 }
 
-void dfree(alto_tensor *h, void *p, size_t bytes, cudaStream_t s) {
+void alto::dfree(alto_tensor *h, void *p, size_t bytes, cudaStream_t s) {
   if (!p) return;
   if (bytes == 0) bytes = 16;
   if (h->user_alloc)
@@ -64,6 +62,8 @@ void dfree(alto_tensor *h, void *p, size_t bytes, cudaStream_t s) {
     cudaFreeAsync(p, s);
   h->bytes_held -= bytes;
 }
+
+namespace {
 
 cudaEvent_t prof_event(alto_tensor *h) {
   if (!h->prof_pool.empty()) {
@@ -348,10 +348,10 @@ alto_status ensure_pull(alto_tensor *h, int n, cudaStream_t s) {
 }
 
 // Hash table of the first nslots hot rows of mode n (open addressing).
-alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) {
-  HotTable &ht = h->hot_tab[n];
+alto_status build_hot_table(alto_tensor *h, int n, int nslots, HotTable &ht, cudaStream_t s) {
   if (ht.nslots == nslots && ht.htab) return ALTO_OK;
-  free_hot(h, n, s);
+  if (ht.htab) dfree(h, ht.htab, ((size_t)1 << ht.hbits) * sizeof(uint64_t), s);
+  ht = HotTable();
   int hbits = 1;
   while ((1 << hbits) < 2 * std::max(nslots, 1)) ++hbits;
   const size_t hsize = (size_t)1 << hbits;
@@ -371,12 +371,15 @@ alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) 
   return ALTO_OK;
 }
 
+alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) {
+  return build_hot_table(h, n, nslots, h->hot_tab[n], s);
+}
+
 bool rank_ok(int R) { return R == 4 || R == 8 || R == 16 || R == 32 || R == 64; }
 
 size_t stage_budget() { return mttkrp_stage_budget(); }
 
-int hot_slots_that_fit(int R, int want) {
-  const size_t budget = stage_budget();
+int hot_slots_within(int R, int want, size_t budget) {
   int k = want;
   while (k > 0) {
     int hbits = 1;
@@ -385,6 +388,20 @@ int hot_slots_that_fit(int R, int want) {
     k = k * 7 / 8;
   }
   return std::max(k, 0);
+}
+
+// Hot rows outside the table take every one of their updates as a global
+// atomic, summed in fp32 in arrival order; a table of at least kMinHotSlots
+// rows keeps those rows' update counts (and so their rounding) small on skewed
+// modes. The table fits the shared memory of kMttkrpBlocksPerSm CTAs per SM
+// when it can; a larger one runs fewer CTAs per SM.
+constexpr int kMinHotSlots = 512;
+
+int hot_slots_that_fit(int R, int want) {
+  int k = hot_slots_within(R, want, stage_budget());
+  const int kmin = std::min(want, kMinHotSlots);
+  if (k < kmin) k = hot_slots_within(R, kmin, mttkrp_smem_limit());
+  return k;
 }
 
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
@@ -397,7 +414,7 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   if (p.cols_per_lane == R && R < 8) p.cols_per_lane = 4;
   if (p.cols_per_lane > 16 && p.cols_per_lane != R) p.cols_per_lane = 16;
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
-  const bool pull_fits = pull_smem <= stage_budget() && h->M > 0;
+  const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
     const double reuse = (double)h->M / (double)h->dims[mode];
     p.variant = (reuse > 4.0 && pull_fits) ? ALTO_VARIANT_PULL
@@ -511,6 +528,27 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace
+
+alto_status alto::repartition(alto_tensor *h, uint64_t L, cudaStream_t s) {
+  return run_partition(h, L, s);
+}
+
+alto_status alto::ensure_group_hot(alto_tensor *h, int n, int nslots, cudaStream_t s,
+                                   const HotTable **out) {
+  nslots = std::min<int>(nslots, (int)h->nhot[n]);
+  HotTable *slot = nullptr;
+  for (HotTable &t : h->group_hot[n]) {
+    if (t.htab && t.nslots == nslots) {
+      *out = &t;
+      return ALTO_OK;
+    }
+    if (!t.htab && !slot) slot = &t;
+  }
+  if (!slot) slot = &h->group_hot[n][0];  // more than five sizes: reuse the first
+  alto_status st = build_hot_table(h, n, nslots, *slot, s);
+  *out = slot;
+  return st;
+}
 
 extern "C" {
 
@@ -725,6 +763,8 @@ void alto_free(alto_handle_t h) {
   for (int n = 0; n < kMaxModes; ++n) {
     free_pull(h, n, s);
     free_hot(h, n, s);
+    for (HotTable &t : h->group_hot[n])
+      if (t.htab) dfree(h, t.htab, ((size_t)1 << t.hbits) * sizeof(uint64_t), s);
     if (h->hot_rows[n]) dfree(h, h->hot_rows[n], ALTO_MAX_HOT * 4, s);
   }
   dfree(h, h->partials.p, h->partials.bytes, s);
@@ -736,6 +776,7 @@ void alto_free(alto_handle_t h) {
   dfree(h, h->status_dev, 4 * 4, s);
   dfree(h, h->norm_sq_dev, 8, s);
   dfree(h, h->nhot_dev, kMaxModes * 4, s);
+  dfree(h, h->dp_rank_dev, sizeof(DecodePlan32), s);
   delete h;
 }
 
@@ -1058,6 +1099,127 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
     return finish(fail(ALTO_ERR_NOT_SPD, "V of Alg. 1 is not positive definite"));
   }
   return finish(ALTO_OK);
+}
+
+alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, alto_dtype fdtype,
+                          float *out, int flags, void *stream, alto_tune_result *res) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  if (!factors || !out || !res) return fail(ALTO_ERR_INVALID_ARG, "factors/out/res NULL");
+  if (fdtype != ALTO_F32 && fdtype != ALTO_BF16) return fail(ALTO_ERR_INVALID_ARG, "bad dtype");
+  for (int m = 0; m < h->N; ++m)
+    if (!factors[m] || !aligned16(factors[m]))
+      return fail(ALTO_ERR_INVALID_ARG, "factors[%d] NULL or not 16-byte aligned", m);
+  if (!aligned16(out)) return fail(ALTO_ERR_INVALID_ARG, "out not 16-byte aligned");
+  *res = alto_tune_result{};
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  const int N = h->N;
+  const bool bf16 = fdtype == ALTO_BF16;
+  for (int n = 0; n < N; ++n) {
+    alto_mode_plan auto_plan{ALTO_VARIANT_AUTO, 0, -1};
+    h->plan[n] = auto_plan;
+  }
+  if (h->M == 0) {
+    for (int n = 0; n < N; ++n) resolve_plan(h, n, R, &res->plan[n]);
+    res->nparts = h->L;
+    return ALTO_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  auto done = [&](alto_status code) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return code;
+  };
+  // one warm-up run, then the faster of two timed runs
+  auto time_plan = [&](int n, const alto_mode_plan &p, double *ms) -> alto_status {
+    h->plan[n] = p;
+    alto_status st2 = mttkrp_impl(h, n, factors, bf16, R, out, s);
+    if (st2 != ALTO_OK) return st2;
+    double best = 1e30;
+    for (int r = 0; r < 2; ++r) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return fail(ALTO_ERR_CUDA, "event");
+      st2 = mttkrp_impl(h, n, factors, bf16, R, out, s);
+      if (st2 != ALTO_OK) return st2;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        return fail(ALTO_ERR_CUDA, "event");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, (double)t);
+    }
+    *ms = best;
+    return ALTO_OK;
+  };
+  const uint64_t L0 = h->L;
+  std::vector<uint64_t> Ls{L0};
+  if (flags & ALTO_TUNE_SEGMENTS) {
+    for (uint64_t seg : {4096ull, 16384ull, 65536ull}) {
+      uint64_t L = std::max<uint64_t>(1, (h->M + seg - 1) / seg);
+      if (std::find(Ls.begin(), Ls.end(), L) == Ls.end()) Ls.push_back(L);
+    }
+  }
+  double best_total = 1e300;
+  uint64_t best_L = L0;
+  alto_mode_plan best_plan[kMaxModes];
+  double best_ms[kMaxModes] = {};
+  int timed = 0;
+  for (uint64_t L : Ls) {
+    if (L != h->L && (st = run_partition(h, L, s)) != ALTO_OK) return done(st);
+    double total = 0.0;
+    alto_mode_plan plan_L[kMaxModes];
+    double ms_L[kMaxModes];
+    for (int n = 0; n < N; ++n) {
+      std::vector<alto_mode_plan> cands;
+      const int cpls[2] = {4, 8};
+      for (int c : cpls)
+        if (R % c == 0 && c < R) cands.push_back(alto_mode_plan{ALTO_VARIANT_ATOMIC, c, -1});
+      const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[n]);
+      if (pull_smem <= mttkrp_smem_limit())
+        for (int c : cpls)
+          if (R % c == 0 && c < R) cands.push_back(alto_mode_plan{ALTO_VARIANT_PULL, c, -1});
+      if (cands.empty()) cands.push_back(alto_mode_plan{ALTO_VARIANT_AUTO, 0, -1});
+      double bms = 1e300;
+      alto_mode_plan bp{};
+      for (const alto_mode_plan &p : cands) {
+        double ms = 0.0;
+        if ((st = time_plan(n, p, &ms)) != ALTO_OK) return done(st);
+        ++timed;
+        if (ms < bms) {
+          bms = ms;
+          bp = p;
+        }
+      }
+      if (L == L0) {
+        double dms = 0.0;
+        if ((st = time_plan(n, alto_mode_plan{ALTO_VARIANT_AUTO, 0, -1}, &dms)) != ALTO_OK)
+          return done(st);
+        res->default_ms[n] = dms;
+      }
+      plan_L[n] = bp;
+      ms_L[n] = bms;
+      total += bms;
+    }
+    if (total < best_total) {
+      best_total = total;
+      best_L = L;
+      for (int n = 0; n < N; ++n) {
+        best_plan[n] = plan_L[n];
+        best_ms[n] = ms_L[n];
+      }
+    }
+  }
+  if (h->L != best_L && (st = run_partition(h, best_L, s)) != ALTO_OK) return done(st);
+  for (int n = 0; n < N; ++n) {
+    h->plan[n] = best_plan[n];
+    resolve_plan(h, n, R, &res->plan[n]);
+    res->ms[n] = best_ms[n];
+  }
+  res->nparts = best_L;
+  res->candidates = timed;
+  return done(ALTO_OK);
 }
 
 }  // extern "C"

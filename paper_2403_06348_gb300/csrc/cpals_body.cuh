@@ -1,0 +1,271 @@
+// Device bodies of the CP-ALS glue kernels (Alg. 1), shared by the
+// one-tensor kernels (cpals.cu) and the CP-ALS batch (batch.cu). Every body
+// is run by all threads of one CTA of kUpdThreads (256) threads.
+#pragma once
+
+#include "cpals.cuh"
+
+namespace alto {
+
+constexpr int kUpdThreads = 256;
+
+// Shared memory of update_body at rank R.
+inline size_t update_smem(int R) {
+  const int TR = 4096 / R;
+  return (size_t)(R * R + R) * sizeof(double) +
+         (size_t)(R * R + R * (TR + 4) + TR * (R + 4)) * sizeof(float);
+}
+
+// V = Hadamard product of the other modes' Grams, its Cholesky factor L
+// (V = L L^T), X = L^-1, V^-1 = X^T X and W = diag(Sn) V^-1, all in fp64
+// inside one CTA. Every elimination step is one pass over the R x R square
+// followed by one barrier: a thread recomputes the pivot quantities it needs
+// from values that are final before the step, and each step writes only
+// entries that no thread reads in that step.
+// sd: 3 R^2 doubles of shared memory.
+__device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
+  if (*a.done_at <= a.it) return;
+  const int R = a.R, RR = R * R, tid = threadIdx.x, nt = blockDim.x;
+  const int lgR = __ffs(R) - 1;
+  double *V = sd;       // V; after the factorisation, X = L^-1
+  double *L = V + RR;   // Cholesky factor (lower)
+  double *Y = L + RR;   // forward-substitution work; then V^-1
+  for (int e = tid; e < RR; e += nt) {
+    double v = 1.0;
+    for (int m = 0; m < a.N; ++m)
+      if (m != a.n) v *= a.G[(size_t)m * RR + e];
+    V[e] = v;
+    Y[e] = ((e >> lgR) == (e & (R - 1))) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // Cholesky, right-looking: step k writes column k of L and updates the
+  // trailing lower triangle (i >= j > k) of V from column k of V.
+  for (int k = 0; k < R; ++k) {
+    const double d = V[k * R + k];
+    if (!(d > 0.0) || !isfinite(d)) {  // the same d in every thread
+      if (tid == 0) {
+        atomicOr(a.status, kStatusNotSpd);
+        *a.done_at = a.it;
+      }
+      return;
+    }
+    const double inv_d = 1.0 / d, rs = rsqrt(d);
+    for (int e = tid; e < RR; e += nt) {
+      const int i = e >> lgR, j = e & (R - 1);
+      if (j == k) {
+        if (i >= k) L[e] = V[e] * rs;
+      } else if (j > k && j <= i) {
+        V[e] -= V[i * R + k] * V[j * R + k] * inv_d;
+      }
+    }
+    __syncthreads();
+  }
+  // X = L^-1 by forward substitution on Y = I: step k finalises row k of X
+  // (into V) and removes column k of L from the rows below.
+  for (int k = 0; k < R; ++k) {
+    const double inv = 1.0 / L[k * R + k];
+    for (int e = tid; e < RR; e += nt) {
+      const int i = e >> lgR, c = e & (R - 1);
+      if (c > k || i < k) continue;
+      const double xk = Y[k * R + c] * inv;
+      if (i == k) V[e] = xk;
+      else Y[e] -= L[i * R + k] * xk;
+    }
+    __syncthreads();
+  }
+  // V^-1 = X^T X (X lower triangular): entry (p, q) sums rows k >= max(p, q)
+  for (int e = tid; e < RR; e += nt) {
+    const int p = e >> lgR, q = e & (R - 1);
+    if (q > p) continue;
+    double acc = 0.0;
+    for (int k = p; k < R; ++k) acc += V[k * R + p] * V[k * R + q];
+    Y[p * R + q] = acc;
+    Y[q * R + p] = acc;
+  }
+  for (int r = tid; r < R; r += nt) {
+    double p = 1.0;
+    for (int m = 0; m < a.N; ++m)
+      if (m != a.n) p *= a.s[(size_t)m * R + r];
+    a.Sn[r] = p;
+  }
+  __syncthreads();
+  for (int e = tid; e < RR; e += nt) a.W[e] = (float)(a.Sn[e >> lgR] * Y[e]);
+}
+
+// B = M W with B^T B and the column dot products of M and B, one pass.
+// A tile of TR = 4096 / R rows: every thread computes a 4-row x 4-column block
+// of B from the transposed M tile and W (two 16-byte shared loads per 16
+// FMAs), adds its block's column products M(r,c) B(r,c), stores B, and then
+// accumulates a 4 x 4 block of B^T B over its share of the tile's rows.
+// fp32 partial sums cover at most 32 tiles per thread before they move to
+// fp64. The CTA walks tiles t0, t0 + tstep, ... < t1 (TR rows each); with
+// clear_m it also zeroes the M rows it has read.
+
+__device__ __forceinline__ void update_body(float *M, const float *__restrict__ W,
+                                            float *__restrict__ Bout, uint64_t I, int R,
+                                            double *__restrict__ BtB, double *__restrict__ dot,
+                                            uint64_t t0, uint64_t tstep, uint64_t t1, bool clear_m,
+                                            unsigned char *smraw) {
+  __syncthreads();  // shared memory may still be read by a previous call
+  const int TR = 4096 / R;       // rows per tile
+  const int TRP = TR + 4;        // padded row count of the transposed tile
+  const int RP = R + 4;          // padded row length of the B tile
+  double *red = reinterpret_cast<double *>(smraw);       // R*R + R
+  float *w = reinterpret_cast<float *>(red + R * R + R);  // R*R
+  float *mt = w + R * R;                                  // R * TRP (M tile, transposed)
+  float *bt = mt + R * TRP;                               // TR * RP (B tile)
+  const int tid = threadIdx.x;
+  const int B4 = R / 4;                      // column blocks
+  const int cb = tid % B4, rb = tid / B4;    // phase 1: rows 4*rb .. 4*rb+3, cols 4*cb ..
+  const int BB = B4 * B4, RG = kUpdThreads / BB;
+  const int tb = tid % BB, rg = tid / BB, bi = tb / B4, bj = tb % B4;
+  for (int i = tid; i < R * R + R; i += kUpdThreads) red[i] = 0.0;
+  for (int i = tid; i < R * R; i += kUpdThreads) w[i] = W[i];
+  float g[4][4], dp[4];
+  double dg[4][4], ddp[4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    dp[x] = 0.f;
+    ddp[x] = 0.0;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      g[x][y] = 0.f;
+      dg[x][y] = 0.0;
+    }
+  }
+  int tiles = 0;
+  float4 *M4 = reinterpret_cast<float4 *>(M);
+  for (uint64_t t = t0; t < t1; t += tstep) {
+    const uint64_t r0 = t * (uint64_t)TR;
+    const int nrows = (I - r0) < (uint64_t)TR ? (int)(I - r0) : TR;
+    __syncthreads();
+    // transpose the M tile into shared memory (rows beyond nrows are zero)
+    for (int i = tid; i < TR * B4; i += kUpdThreads) {
+      const int r = i / B4, c = (i - r * B4) * 4;
+      const float4 m = r < nrows ? M4[(r0 + r) * B4 + (i - r * B4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (clear_m && r < nrows) M4[(r0 + r) * B4 + (i - r * B4)] = make_float4(0.f, 0.f, 0.f, 0.f);
+      mt[(c + 0) * TRP + r] = m.x;
+      mt[(c + 1) * TRP + r] = m.y;
+      mt[(c + 2) * TRP + r] = m.z;
+      mt[(c + 3) * TRP + r] = m.w;
+    }
+    __syncthreads();
+    float o[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
+    for (int k = 0; k < R; ++k) {
+      const float4 mk = *reinterpret_cast<const float4 *>(mt + k * TRP + 4 * rb);
+      const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + 4 * cb);
+      const float ma[4] = {mk.x, mk.y, mk.z, mk.w}, wa[4] = {wk.x, wk.y, wk.z, wk.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o[x][y] = fmaf(ma[x], wa[y], o[x][y]);
+    }
+    // column products with M, store B (global and shared)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const float4 mc = *reinterpret_cast<const float4 *>(mt + (4 * cb + y) * TRP + 4 * rb);
+      const float ma[4] = {mc.x, mc.y, mc.z, mc.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x) dp[y] = fmaf(ma[x], o[x][y], dp[y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int r = 4 * rb + x;
+      const float4 ov = make_float4(o[x][0], o[x][1], o[x][2], o[x][3]);
+      *reinterpret_cast<float4 *>(bt + r * RP + 4 * cb) = ov;
+      if (r < nrows) *reinterpret_cast<float4 *>(Bout + (r0 + r) * (uint64_t)R + 4 * cb) = ov;
+    }
+    __syncthreads();
+    for (int r = rg; r < nrows; r += RG) {
+      const float4 xv = *reinterpret_cast<const float4 *>(bt + r * RP + 4 * bi);
+      const float4 yv = *reinterpret_cast<const float4 *>(bt + r * RP + 4 * bj);
+      const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) g[x][y] = fmaf(xa[x], ya[y], g[x][y]);
+    }
+    if (++tiles == 32) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        ddp[x] += (double)dp[x];
+        dp[x] = 0.f;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          dg[x][y] += (double)g[x][y];
+          g[x][y] = 0.f;
+        }
+      }
+      tiles = 0;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      dg[x][y] += (double)g[x][y];
+      atomicAdd(&red[(4 * bi + x) * R + 4 * bj + y], dg[x][y]);
+    }
+    atomicAdd(&red[R * R + 4 * cb + x], ddp[x] + (double)dp[x]);
+  }
+  __syncthreads();
+  for (int i = tid; i < R * R; i += kUpdThreads)
+    if (red[i] != 0.0) atomicAdd(&BtB[i], red[i]);
+  for (int i = tid; i < R; i += kUpdThreads)
+    if (red[R * R + i] != 0.0) atomicAdd(&dot[i], red[R * R + i]);
+}
+
+__device__ __forceinline__ void finish_body(const CpArgs &a) {
+  if (*a.done_at <= a.it) return;
+  const int R = a.R, RR = R * R, tid = threadIdx.x;
+  __shared__ double lam[ALTO_MAX_RANK], sn[ALTO_MAX_RANK];
+  __shared__ double part[2][256];
+  double *sv = a.s + (size_t)a.n * R;
+  double *Gn = a.G + (size_t)a.n * RR;
+  for (int r = tid; r < R; r += blockDim.x) {
+    const double g = a.BtB[r * R + r];
+    const double l = g > 0.0 ? sqrt(g) : 0.0;
+    lam[r] = l;
+    sn[r] = l > 0.0 ? 1.0 / l : 1.0;
+    a.lambda[r] = l;
+    sv[r] = sn[r];
+  }
+  __syncthreads();
+  for (int e = tid; e < RR; e += blockDim.x) Gn[e] = a.BtB[e] * sn[e / R] * sn[e % R];
+  __syncthreads();
+  if (!a.last_mode) return;
+  // fit = 1 - sqrt(max(0, ||X||^2 + lam^T (*_m G_m) lam - 2 <X, X_hat>)) / ||X||,
+  // <X, X_hat> = sum_r lam_r sum_i M(i,r) A_n(i,r) = sum_r Sn_r sum_i M_B(i,r) B_n(i,r)
+  double s1 = 0.0, s2 = 0.0;
+  for (int e = tid; e < RR; e += blockDim.x) {
+    double h = 1.0;
+    for (int m = 0; m < a.N; ++m) h *= a.G[(size_t)m * RR + e];
+    s1 += lam[e / R] * lam[e % R] * h;
+  }
+  for (int r = tid; r < R; r += blockDim.x) s2 += a.Sn[r] * a.dot[r];
+  part[0][tid] = s1;
+  part[1][tid] = s2;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) {
+      part[0][tid] += part[0][tid + o];
+      part[1][tid] += part[1][tid + o];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double nx = *a.norm_sq;
+    const double resid = nx + part[0][0] - 2.0 * part[1][0];
+    const double fit = nx > 0.0 ? 1.0 - sqrt(resid > 0.0 ? resid : 0.0) / sqrt(nx) : 0.0;
+    a.fits[a.it] = fit;
+    *a.iters_done = a.it + 1;
+    if (a.tol > 0.0 && a.it > 0 && fabs(fit - a.fits[a.it - 1]) < a.tol) *a.done_at = a.it + 1;
+  }
+}
+
+}  // namespace alto

@@ -8,6 +8,8 @@
 
 #include "alto_internal.cuh"
 
+struct alto_tensor;
+
 namespace alto {
 
 // Sets the calling thread's error message (alto_last_error) and returns st.
@@ -46,6 +48,25 @@ struct Buf {
 
 }  // namespace alto
 
+namespace alto {
+
+// Device memory of a handle: its allocator if it has one, else
+// cudaMallocAsync / cudaFreeAsync on stream s; counted in bytes_held.
+void *dalloc(alto_tensor *h, size_t bytes, cudaStream_t s);
+void dfree(alto_tensor *h, void *p, size_t bytes, cudaStream_t s);
+
+// Re-partitions the handle into L segments (Section IV-A) on stream s; waits
+// for s (the interval lengths come back to the host).
+alto_status repartition(alto_tensor *h, uint64_t L, cudaStream_t s);
+
+// A hot-row table of mode n for grouped launches holding the first nslots
+// sampled hot rows (at most the number sampled); tables of up to five sizes
+// are kept in the handle until alto_free. Waits for s.
+alto_status ensure_group_hot(alto_tensor *h, int n, int nslots, cudaStream_t s,
+                             const HotTable **out);
+
+}  // namespace alto
+
 struct alto_tensor {
   using DecodePlan = alto::DecodePlan;
   using DecodePlan32 = alto::DecodePlan32;
@@ -78,6 +99,7 @@ struct alto_tensor {
   uint32_t *max_len_dev = nullptr;
   uint32_t *status_dev = nullptr;
   double *norm_sq_dev = nullptr;
+  DecodePlan32 *dp_rank_dev = nullptr;   // runs by rank, for grouped launches
   uint32_t *hot_rows[alto::kMaxModes] = {};
   uint32_t *nhot_dev = nullptr;
   // host mirrors
@@ -90,6 +112,7 @@ struct alto_tensor {
   // plans and caches
   alto_mode_plan plan[alto::kMaxModes];
   HotTable hot_tab[alto::kMaxModes];
+  HotTable group_hot[alto::kMaxModes][5];  // smaller tables for grouped launches, by size
   PullPlan pull[alto::kMaxModes];
   Buf partials;
   // instrumentation

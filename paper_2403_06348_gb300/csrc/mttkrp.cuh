@@ -6,11 +6,13 @@
 namespace alto {
 
 // Persistent CTAs: kMttkrpBlocksPerSm CTAs of kMttkrpThreads threads per SM.
+// Three CTAs of 512 threads (48 warps, at most 40 registers a thread) hide
+// more gather latency than one CTA of 1024 threads at 64 registers.
 #ifndef ALTO_MTTKRP_THREADS
-#define ALTO_MTTKRP_THREADS 1024
+#define ALTO_MTTKRP_THREADS 512
 #endif
 #ifndef ALTO_MTTKRP_BLOCKS_PER_SM
-#define ALTO_MTTKRP_BLOCKS_PER_SM 1
+#define ALTO_MTTKRP_BLOCKS_PER_SM 3
 #endif
 constexpr int kMttkrpThreads = ALTO_MTTKRP_THREADS;
 constexpr int kMttkrpBlocksPerSm = ALTO_MTTKRP_BLOCKS_PER_SM;

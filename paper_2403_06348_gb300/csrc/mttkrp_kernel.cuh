@@ -162,14 +162,15 @@ __device__ __forceinline__ void decode_blocks(const BlockPlan &bp, uint64_t lo, 
 // j = grp * tpn + q; the group gathers its N-1 input rows (lane `sub` holds the
 // column vectors sub, sub + tpn, ...), multiplies, and sums runs of equal
 // output row in registers before flushing them. TAIL batches check j < nvalid.
+// fb[k] is the k-th input factor plus this lane's byte offset (inb).
 template <int NMAX, int CPL, bool BF16, bool TAIL>
-__device__ __forceinline__ void group_rounds(const MttkrpArgs &a, int N, int tpn, int grp, int sub,
+__device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? NMAX - 1 : 1],
+                                             float *out, int R, int N, int tpn, int grp, int sub,
                                              float v, int slot, uint32_t row,
                                              const uint32_t (&in)[NMAX > 1 ? NMAX - 1 : 1], int nvalid,
-                                             float *temp, uint32_t rowb, uint32_t inb) {
+                                             float *temp, uint32_t rowb) {
   constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
   const unsigned full = 0xffffffffu;
-  const int R = a.R;
   float run[CPL];
 #pragma unroll
   for (int k = 0; k < CPL; ++k) run[k] = 0.f;
@@ -189,7 +190,7 @@ __device__ __forceinline__ void group_rounds(const MttkrpArgs &a, int N, int tpn
 #pragma unroll
     for (int k = 0; k < NIN; ++k) {
       if (k + 1 < N) {
-        const char *rb = static_cast<const char *>(a.fin[k]) + (uint64_t)ij[k] * rowb + inb;
+        const char *rb = fb[k] + (uint64_t)ij[k] * rowb;
         float f[CPL];
 #pragma unroll
         for (int w = 0; w < CPL / 4; ++w) {
@@ -219,14 +220,14 @@ __device__ __forceinline__ void group_rounds(const MttkrpArgs &a, int N, int tpn
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] += p[c];
     } else {
-      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, a.out, R, sub, tpn);
+      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] = p[c];
       run_row = rj;
       run_slot = sj;
     }
   }
-  if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, a.out, R, sub, tpn);
+  if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn);
 }
 
 template <int NT, int KW, int CPL, bool BF16, bool PULL>
@@ -243,6 +244,10 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
   // byte offset of this lane's first column vector, and the row strides
   const uint32_t rowb = (uint32_t)R * (BF16 ? 2u : 4u);
   const uint32_t inb = 4u * (uint32_t)sub * (BF16 ? 2u : 4u);
+  constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
+  const char *fb[NIN];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) fb[k] = static_cast<const char *>(a.fin[k]) + inb;
 
   uint64_t *htab = nullptr;
   if (!PULL) {
@@ -293,7 +298,6 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
       else
         decode_runs<KW, NMAX>(a.dp, N, lo, hi, c);
       // the output row and the N-1 input coordinates in a fixed order
-      constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
       uint32_t row = c[0];
       uint32_t in[NIN];
 #pragma unroll
@@ -305,11 +309,11 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
       if (valid) slot = PULL ? (int)(row - Ts) : hot_lookup(htab, a.hbits, row);
       const uint64_t rem = s1 - base;
       if (rem >= 32)
-        group_rounds<NMAX, CPL, BF16, false>(a, N, tpn, grp, sub, v, slot, row, in, 32, temp, rowb,
-                                             inb);
+        group_rounds<NMAX, CPL, BF16, false>(fb, a.out, R, N, tpn, grp, sub, v, slot, row, in, 32,
+                                             temp, rowb);
       else
-        group_rounds<NMAX, CPL, BF16, true>(a, N, tpn, grp, sub, v, slot, row, in, (int)rem, temp,
-                                            rowb, inb);
+        group_rounds<NMAX, CPL, BF16, true>(fb, a.out, R, N, tpn, grp, sub, v, slot, row, in,
+                                            (int)rem, temp, rowb);
     }
     if (PULL) {
       __syncthreads();
@@ -477,6 +481,18 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm)
   }
 }
 
+// CTAs of kMttkrpThreads that fit one SM with `smem` bytes of dynamic shared
+// memory (at most kMttkrpBlocksPerSm).
+template <typename K>
+static int resident_ctas(K kern, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMttkrpThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm < 1 ? 1 : (per_sm > kMttkrpBlocksPerSm ? kMttkrpBlocksPerSm : per_sm);
+}
+
 template <int NT, int KW, bool BF16, bool PULL>
 static cudaError_t launch_lpn(const MttkrpArgs &a, size_t smem, int num_sms, cudaStream_t s) {
   auto kern = mttkrp_lpn_kernel<NT, KW, BF16, PULL>;
@@ -487,7 +503,7 @@ static cudaError_t launch_lpn(const MttkrpArgs &a, size_t smem, int num_sms, cud
     if (e != cudaSuccess) return e;
     configured = 1;
   }
-  uint64_t grid = (uint64_t)num_sms * kMttkrpBlocksPerSm;
+  uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, smem);
   if (grid > a.L) grid = a.L;
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, kMttkrpThreads, smem, s>>>(a);
@@ -515,7 +531,7 @@ static cudaError_t launch_one(const MttkrpArgs &a, size_t smem, int num_sms, cud
     if (e != cudaSuccess) return e;
     configured = 1;
   }
-  uint64_t grid = (uint64_t)num_sms * kMttkrpBlocksPerSm;
+  uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, smem);
   if (grid > a.L) grid = a.L;
   if (grid < 1) grid = 1;
   kern<<<(unsigned)grid, kMttkrpThreads, smem, s>>>(a);

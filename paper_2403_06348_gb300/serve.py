@@ -1,0 +1,300 @@
+"""CP-ALS serving on one GPU: continuous batching over the library's CP-ALS batch.
+
+``Server.submit`` takes a COO tensor (host arrays) and CP-ALS parameters and
+returns a Future. An admission thread encodes requests on its own stream
+(alto_encode) as device memory allows: a request is admitted while the
+resident bytes of the runs in flight plus its own peak bytes
+(alto_cpals_footprint) stay within the budget and a batch slot is free. The
+loop thread adds encoded requests to the batch, advances every active run by
+one mode update per step (alto_batch_step, a replayed CUDA graph), polls the
+asynchronous state read-backs, and retires finished runs (normalised factors,
+lambda and fits copied into pinned host memory). Requests that arrive while
+others are on the GPU join at the next step, so their work overlaps.
+
+``run_fcfs`` is the one-at-a-time reference: the same library, one request
+after the other in arrival order, each encoded and solved with cpals_run.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from concurrent.futures import Future
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import AltoError, Batch, alto_cpals_footprint, alto_encode, alto_fill_uniform
+
+
+@dataclasses.dataclass
+class CPResult:
+    factors: List[np.ndarray]
+    lam: np.ndarray
+    fits: List[float]
+    iters_done: int
+    status: int
+    arrival: float
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclasses.dataclass
+class _Request:
+    coords: np.ndarray
+    vals: np.ndarray
+    dims: tuple
+    R: int
+    iters: int
+    tol: float
+    init: List[np.ndarray]
+    arrival: float
+    future: Future
+    peak: int = 0
+    resident: int = 0
+    tensor: object = None
+    admitted: float = 0.0
+    seed: int = 0
+
+
+def device_factors(dims: Sequence[int], R: int, seed: int, stream=None):
+    """Initial factors drawn on the GPU: factor m = alto_fill_uniform(seed * 16 + m)."""
+    import torch
+    out = []
+    for m, d in enumerate(dims):
+        a = torch.empty((int(d), int(R)), dtype=torch.float32, device="cuda")
+        alto_fill_uniform(a, (int(seed) * 16 + m) % (1 << 32), stream)
+        out.append(a)
+    return out
+
+
+def percentile(xs: Sequence[float], q: float) -> float:
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else float("nan")
+
+
+class Server:
+    """Continuous-batching CP-ALS server (see module docstring)."""
+
+    def __init__(self, budget_bytes: float = 100e9, max_slots: int = 1024, steps_per_round: int = 4):
+        import torch
+        self.budget = int(budget_bytes)
+        self.max_slots = int(max_slots)
+        self.steps_per_round = int(steps_per_round)
+        self.batch = Batch(max_slots=max_slots)
+        self.encode_stream = torch.cuda.Stream()
+        self._lock = threading.Condition()
+        self._waiting: collections.deque = collections.deque()   # submitted, not encoded
+        self._ready: collections.deque = collections.deque()     # encoded, not in the batch
+        self._live = {}                                          # slot -> request
+        self._retiring: list = []                                # (event, request, buffers)
+        self._resident = 0
+        self._admitted = 0
+        self._stop = False
+        self.latencies: List[float] = []
+        self.completed = 0
+        self.errors = 0
+        self.work_nnz_r_iters = 0.0
+        self.t_first: Optional[float] = None
+        self.t_last: Optional[float] = None
+        self._admit_thread = threading.Thread(target=self._admit_loop, daemon=True)
+        self._loop_thread = threading.Thread(target=self._loop, daemon=True)
+        self._admit_thread.start()
+        self._loop_thread.start()
+
+    # -- public --------------------------------------------------------------
+    def submit(self, coords: np.ndarray, vals: np.ndarray, dims: Sequence[int], R: int, iters: int,
+               init: Optional[Sequence[np.ndarray]] = None, seed: int = 0, tol: float = 0.0,
+               arrival: Optional[float] = None) -> Future:
+        """``init``: host initial factors, or None to draw them on the GPU from
+        ``seed`` (factor m filled by alto_fill_uniform with seed * 16 + m)."""
+        fut: Future = Future()
+        init_l = None if init is None else [np.ascontiguousarray(a, dtype=np.float32) for a in init]
+        req = _Request(np.asarray(coords), np.asarray(vals, dtype=np.float32), tuple(int(d) for d in dims),
+                       int(R), int(iters), float(tol), init_l,
+                       time.perf_counter() if arrival is None else arrival, fut)
+        req.seed = int(seed)
+        req.resident, req.peak = alto_cpals_footprint(req.dims, req.vals.shape[0], req.R, req.iters)
+        with self._lock:
+            if self.t_first is None:
+                self.t_first = req.arrival
+            self._waiting.append(req)
+            self._lock.notify_all()
+        return fut
+
+    def close(self, timeout: Optional[float] = None) -> None:
+        with self._lock:
+            self._stop = True
+            self._lock.notify_all()
+        self._admit_thread.join(timeout)
+        self._loop_thread.join(timeout)
+        self.batch.free()
+
+    def stats(self) -> dict:
+        span = (self.t_last - self.t_first) if (self.t_first is not None and self.t_last) else float("nan")
+        return {"completed": self.completed, "errors": self.errors,
+                "p50_s": percentile(self.latencies, 50), "p99_s": percentile(self.latencies, 99),
+                "mean_s": float(np.mean(self.latencies)) if self.latencies else float("nan"),
+                "requests_per_s": self.completed / span if span and span > 0 else float("nan"),
+                "nnz_r_iters_per_s": self.work_nnz_r_iters / span if span and span > 0 else float("nan"),
+                "makespan_s": span}
+
+    # -- admission thread: encode while memory allows ------------------------
+    def _admit_loop(self) -> None:
+        import torch
+        while True:
+            with self._lock:
+                while not self._stop and not self._can_admit():
+                    self._lock.wait(0.002)
+                if self._stop and not self._waiting:
+                    return
+                if not self._can_admit():
+                    continue
+                req = self._waiting.popleft()
+                self._resident += req.resident
+                self._admitted += 1
+            try:
+                with torch.cuda.stream(self.encode_stream):
+                    req.tensor = alto_encode(req.coords, req.vals, req.dims, stream=self.encode_stream)
+                    # initial factors on the encode stream (the batch orders
+                    # itself after the handle's stream)
+                    if req.init is None:
+                        req.init = device_factors(req.dims, req.R, req.seed, self.encode_stream)
+                    else:
+                        req.init = [torch.from_numpy(a).pin_memory().cuda(non_blocking=True)
+                                    for a in req.init]
+                req.admitted = time.perf_counter()
+                with self._lock:
+                    self._ready.append(req)
+                    self._lock.notify_all()
+            except AltoError as e:
+                with self._lock:
+                    self._resident -= req.resident
+                    self._admitted -= 1
+                    self.errors += 1
+                req.future.set_exception(e)
+
+    def _can_admit(self) -> bool:
+        if not self._waiting or self._admitted >= self.max_slots:
+            return False
+        req = self._waiting[0]
+        if self._admitted == 0:
+            return True  # always admit one, even over budget
+        return self._resident + req.peak <= self.budget
+
+    # -- loop thread: batch steps, polls, retirement -------------------------
+    def _loop(self) -> None:
+        import torch
+        while True:
+            with self._lock:
+                ready = list(self._ready)
+                self._ready.clear()
+                idle = not ready and not self._live and not self._retiring
+                if idle:
+                    if self._stop and not self._waiting and self._admitted == 0:
+                        return
+                    self._lock.wait(0.002)
+                    continue
+            for req in ready:
+                try:
+                    slot = self.batch.add(req.tensor, req.R, req.iters, req.init, tol=req.tol)
+                    self._live[slot] = req
+                except AltoError as e:
+                    self._finish_error(req, e)
+            if self._live:
+                self.batch.step(self.steps_per_round)
+                done = self.batch.poll(wait=False)
+                if not done and self.batch.info().pending_readbacks >= 2:
+                    done = self.batch.poll(wait=True)
+                for slot in done:
+                    req = self._live.pop(slot)
+                    outs = [torch.empty((d, req.R), dtype=torch.float32, pin_memory=True) for d in req.dims]
+                    lam = torch.empty(req.R, dtype=torch.float64, pin_memory=True)
+                    fits = torch.zeros(req.iters, dtype=torch.float64, pin_memory=True)
+                    iters_done, status = self.batch.result(slot, outs, lam, fits)
+                    ev = torch.cuda.Event()
+                    ev.record(self.batch.stream)
+                    self.batch.remove(slot)
+                    self._retiring.append((ev, req, outs, lam, fits, iters_done, status))
+            still = []
+            for item in self._retiring:
+                ev, req, outs, lam, fits, iters_done, status = item
+                if not ev.query():
+                    still.append(item)
+                    continue
+                now = time.perf_counter()
+                res = CPResult([o.numpy() for o in outs], lam.numpy(), fits.numpy()[:iters_done].tolist(),
+                               iters_done, status, req.arrival, req.admitted, now)
+                req.tensor.free()
+                req.tensor = None
+                with self._lock:
+                    self._resident -= req.resident
+                    self._admitted -= 1
+                    self.completed += 1
+                    self.latencies.append(res.latency)
+                    self.work_nnz_r_iters += float(req.vals.shape[0]) * req.R * iters_done
+                    self.t_last = now
+                    self._lock.notify_all()
+                req.future.set_result(res)
+            self._retiring = still
+            if not self._live and self._retiring:
+                time.sleep(0.0002)
+
+    def _finish_error(self, req: _Request, e: Exception) -> None:
+        if req.tensor is not None:
+            req.tensor.free()
+        with self._lock:
+            self._resident -= req.resident
+            self._admitted -= 1
+            self.errors += 1
+            self._lock.notify_all()
+        req.future.set_exception(e)
+
+
+def run_fcfs(requests, schedule_start: float) -> dict:
+    """One-at-a-time reference: each request, in arrival order and no earlier
+    than its arrival, encoded and solved alone with cpals_run (ungrouped
+    launches, no graphs), its factors copied back to the host. ``requests``
+    yields (arrival_offset_s, coords, vals, dims, R, iters, init, seed), init
+    None for factors drawn on the GPU as the Server does. Returns latency /
+    throughput statistics."""
+    import torch
+    lat, work = [], 0.0
+    not_spd = 0
+    t_first = t_last = None
+    for arrival_off, coords, vals, dims, R, iters, init, seed in requests:
+        arrival = schedule_start + arrival_off
+        now = time.perf_counter()
+        if now < arrival:
+            time.sleep(arrival - now)
+        if t_first is None:
+            t_first = arrival
+        t = alto_encode(coords, vals, dims)
+        if init is None:
+            A = device_factors(dims, R, seed)
+        else:
+            A = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in init]
+        try:
+            lam, fits = t.cpals(R, iters, A)
+        except AltoError as e:
+            if e.status != -6:  # NOT_SPD ends a run early with its last factors
+                raise
+            not_spd += 1
+            fits = []
+        outs = [torch.empty(a.shape, dtype=torch.float32, pin_memory=True) for a in A]
+        for o, a in zip(outs, A):
+            o.copy_(a)
+        t.free()
+        t_last = time.perf_counter()
+        lat.append(t_last - arrival)
+        work += float(len(vals)) * R * len(fits)
+    span = (t_last - t_first) if t_first is not None else float("nan")
+    return {"completed": len(lat), "not_spd": not_spd,
+            "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99),
+            "mean_s": float(np.mean(lat)) if lat else float("nan"),
+            "requests_per_s": len(lat) / span if span > 0 else float("nan"),
+            "nnz_r_iters_per_s": work / span if span > 0 else float("nan"), "makespan_s": span}

@@ -237,3 +237,37 @@ def request_tensor(req: Request) -> Tuple[np.ndarray, np.ndarray]:
     spec = TensorSpec(f"req{req.rid}", req.dims, req.nnz, ("zipf:1.1",) * len(req.dims),
                       "uniform01", req.rank, seed=req.seed)
     return generate(spec)
+
+
+def request_pool_stream(count: int = 2000, pool: int = 64, rate_per_s: float = 200.0,
+                        seed: int = BASE_SEED + 4, dim_range=(100, 1_000_000),
+                        nnz_range=(1_000, 10_000_000), modes=(3, 4, 5), ranks=(8, 16, 32),
+                        iters: int = 20) -> Tuple[List[Request], List[Request]]:
+    """The serving workload with a bounded amount of tensor data to generate.
+
+    ``pool`` distinct tensors are drawn with their nonzero counts at the
+    midpoints of ``pool`` equal log-spaced bins of ``nnz_range`` (so the pool
+    follows the log-uniform law, mean included) and dims, order and rank drawn
+    as in ``request_stream``. The ``count`` requests arrive as a Poisson
+    stream at ``rate_per_s``; request i uses pool entry perm[i mod pool] of a
+    seeded permutation, with its own rank and initial-factor seed. Returns
+    (pool, requests); a request's ``rid`` is its pool index."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo, hi = math.log(nnz_range[0]), math.log(nnz_range[1])
+    entries = []
+    for j in range(pool):
+        N = int(rng.choice(modes))
+        dims = tuple(int(round(math.exp(rng.uniform(math.log(dim_range[0]),
+                                                    math.log(dim_range[1])))))
+                     for _ in range(N))
+        nnz = int(round(math.exp(lo + (j + 0.5) / pool * (hi - lo))))
+        entries.append(Request(j, 0.0, dims, nnz, int(rng.choice(ranks)), iters,
+                               int(rng.integers(0, 2**31 - 1))))
+    perm = rng.permutation(pool)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, count))
+    reqs = []
+    for i in range(count):
+        e = entries[int(perm[i % pool])]
+        reqs.append(Request(e.rid, float(t[i]), e.dims, e.nnz, int(rng.choice(ranks)), iters,
+                            int(rng.integers(0, 2**31 - 1))))
+    return entries, reqs
