@@ -489,7 +489,7 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     a.partials = static_cast<float *>(h->partials.p);
     a.part_off = pp.part_off;
     const size_t smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
-    if (p.cols_per_lane == R)
+    if (p.cols_per_lane == R || (p.cols_per_lane == 8 && !bf16))
       for (int m = 0; m < h->N; ++m)
         if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
     {
@@ -501,8 +501,9 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
       CUDA_TRY(launch_pull_reduce(a.partials, pp.row_ptr, pp.prow, I, R, out, h->num_sms, s));
     }
   } else {
-    if (p.cols_per_lane == R) {
-      // one thread per nonzero reads 32-byte chunks: factors need 32-byte alignment
+    if (p.cols_per_lane == R || (p.cols_per_lane == 8 && !bf16)) {
+      // 32-byte loads (one thread per nonzero, or 8 columns per lane in fp32):
+      // factors need 32-byte alignment
       for (int m = 0; m < h->N; ++m)
         if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
     }

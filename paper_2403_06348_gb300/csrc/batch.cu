@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kUpdThreads) batch_prepare_kernel(const CpProb
   }
 }
 
-__global__ void __launch_bounds__(kUpdThreads) batch_update_kernel(const CpProb *__restrict__ probs,
+__global__ void __launch_bounds__(kUpdThreads, 2) batch_update_kernel(const CpProb *__restrict__ probs,
                                                                    const CpState *__restrict__ st,
                                                                    const int *__restrict__ tiles,
                                                                    const int *nslots) {

@@ -66,12 +66,15 @@ __global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, 
     }
   }
   __syncthreads();
+  // lanes holding the same block (equal modulo BB) are summed in the warp first
+  const int lane = tid & 31;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      dacc[a][b] += (double)acc[a][b];
-      atomicAdd(&red[(bi * 4 + a) * R + bj * 4 + b], dacc[a][b]);
+      double v = dacc[a][b] + (double)acc[a][b];
+      for (int o = 16; o >= BB; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (BB >= 32 || lane < BB) atomicAdd(&red[(bi * 4 + a) * R + bj * 4 + b], v);
     }
   __syncthreads();
   for (int i = tid; i < R * R; i += 256)
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(256) prepare_kernel(const CpArgs a) {
   prepare_body(a, sd);
 }
 
-__global__ void __launch_bounds__(kUpdThreads) update_kernel(const float *__restrict__ M,
+__global__ void __launch_bounds__(kUpdThreads, 2) update_kernel(const float *__restrict__ M,
                                                              const float *__restrict__ W,
                                                              float *__restrict__ Bout, uint64_t I, int R,
                                                              double *__restrict__ BtB, double *__restrict__ dot,

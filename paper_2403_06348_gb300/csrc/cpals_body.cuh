@@ -30,12 +30,19 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
   double *V = sd;       // V; after the factorisation, X = L^-1
   double *L = V + RR;   // Cholesky factor (lower)
   double *Y = L + RR;   // forward-substitution work; then V^-1
+  // 1/d_k and 1/sqrt(d_k) of each pivot, computed once by the thread that
+  // finalises d_k (fp64 division is slow; every other thread reads them)
+  __shared__ double s_inv[ALTO_MAX_RANK], s_rs[ALTO_MAX_RANK];
   for (int e = tid; e < RR; e += nt) {
     double v = 1.0;
     for (int m = 0; m < a.N; ++m)
       if (m != a.n) v *= a.G[(size_t)m * RR + e];
     V[e] = v;
     Y[e] = ((e >> lgR) == (e & (R - 1))) ? 1.0 : 0.0;
+    if (e == 0 && v > 0.0) {
+      s_inv[0] = 1.0 / v;
+      s_rs[0] = rsqrt(v);
+    }
   }
   __syncthreads();
   // Cholesky, right-looking: step k writes column k of L and updates the
@@ -49,13 +56,18 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
       }
       return;
     }
-    const double inv_d = 1.0 / d, rs = rsqrt(d);
+    const double inv_d = s_inv[k], rs = s_rs[k];
     for (int e = tid; e < RR; e += nt) {
       const int i = e >> lgR, j = e & (R - 1);
       if (j == k) {
         if (i >= k) L[e] = V[e] * rs;
       } else if (j > k && j <= i) {
-        V[e] -= V[i * R + k] * V[j * R + k] * inv_d;
+        const double v = V[e] - V[i * R + k] * V[j * R + k] * inv_d;
+        V[e] = v;
+        if (i == k + 1 && j == k + 1 && v > 0.0) {  // the next pivot
+          s_inv[k + 1] = 1.0 / v;
+          s_rs[k + 1] = rsqrt(v);
+        }
       }
     }
     __syncthreads();
@@ -63,7 +75,7 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
   // X = L^-1 by forward substitution on Y = I: step k finalises row k of X
   // (into V) and removes column k of L from the rows below.
   for (int k = 0; k < R; ++k) {
-    const double inv = 1.0 / L[k * R + k];
+    const double inv = s_rs[k];  // 1 / L[k][k] = 1 / sqrt(d_k)
     for (int e = tid; e < RR; e += nt) {
       const int i = e >> lgR, c = e & (R - 1);
       if (c > k || i < k) continue;
@@ -135,20 +147,37 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
   }
   int tiles = 0;
   float4 *M4 = reinterpret_cast<float4 *>(M);
+  // A tile is TR x R = 4096 floats: kPer 16-byte vectors per thread. The next
+  // tile's vectors are loaded into registers while the current one is used.
+  constexpr int kPer = 4096 / 4 / kUpdThreads;
+  float4 nxt[kPer];
+  auto load_tile = [&](uint64_t tt) {
+    const uint64_t rr0 = tt * (uint64_t)TR;
+    const int nr = (I - rr0) < (uint64_t)TR ? (int)(I - rr0) : TR;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + j * kUpdThreads, r = i / B4;
+      nxt[j] = r < nr ? M4[(rr0 + r) * B4 + (i - r * B4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  if (t0 < t1) load_tile(t0);
   for (uint64_t t = t0; t < t1; t += tstep) {
     const uint64_t r0 = t * (uint64_t)TR;
     const int nrows = (I - r0) < (uint64_t)TR ? (int)(I - r0) : TR;
     __syncthreads();
     // transpose the M tile into shared memory (rows beyond nrows are zero)
-    for (int i = tid; i < TR * B4; i += kUpdThreads) {
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int i = tid + j * kUpdThreads;
       const int r = i / B4, c = (i - r * B4) * 4;
-      const float4 m = r < nrows ? M4[(r0 + r) * B4 + (i - r * B4)] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 m = nxt[j];
       if (clear_m && r < nrows) M4[(r0 + r) * B4 + (i - r * B4)] = make_float4(0.f, 0.f, 0.f, 0.f);
       mt[(c + 0) * TRP + r] = m.x;
       mt[(c + 1) * TRP + r] = m.y;
       mt[(c + 2) * TRP + r] = m.z;
       mt[(c + 3) * TRP + r] = m.w;
     }
+    if (t + tstep < t1) load_tile(t + tstep);
     __syncthreads();
     float o[4][4];
 #pragma unroll
@@ -204,14 +233,22 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
     }
   }
   __syncthreads();
+  // Threads holding the same block of B^T B (the same tb) or the same columns
+  // of the dot products (the same cb) are first summed inside the warp (lanes
+  // equal modulo BB or B4), so at most one shared atomic per warp and address.
+  const unsigned full = 0xffffffffu;
+  const int lane = tid & 31;
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
-      dg[x][y] += (double)g[x][y];
-      atomicAdd(&red[(4 * bi + x) * R + 4 * bj + y], dg[x][y]);
+      double v = dg[x][y] + (double)g[x][y];
+      for (int o = 16; o >= BB; o >>= 1) v += __shfl_xor_sync(full, v, o);
+      if (BB >= 32 || lane < BB) atomicAdd(&red[(4 * bi + x) * R + 4 * bj + y], v);
     }
-    atomicAdd(&red[R * R + 4 * cb + x], ddp[x] + (double)dp[x]);
+    double v = ddp[x] + (double)dp[x];
+    for (int o = 16; o >= B4; o >>= 1) v += __shfl_xor_sync(full, v, o);
+    if (B4 >= 32 || lane < B4) atomicAdd(&red[R * R + 4 * cb + x], v);
   }
   __syncthreads();
   for (int i = tid; i < R * R; i += kUpdThreads)

@@ -70,7 +70,7 @@ __device__ __noinline__ void group_segment(const GroupUnit &g, const DecodePlan3
   const int grp = lane / tpn, sub = lane - grp * tpn;
   const int ro = g.ro;
   const uint32_t rowb = (uint32_t)R * (BF16 ? 2u : 4u);
-  const uint32_t inb = 4u * (uint32_t)sub * (BF16 ? 2u : 4u);
+  const uint32_t inb = lane_byte_offset<CPL, BF16>(sub);
   const char *fb[NIN];
 #pragma unroll
   for (int k = 0; k < NIN; ++k)

@@ -74,23 +74,63 @@ __device__ __forceinline__ int slot_swizzle(int slot, int R) {
   return (slot & m) << 2;
 }
 
+#ifndef ALTO_HOT_ROTATE
+#define ALTO_HOT_ROTATE 1
+#endif
+
+// First column of a lane's v-th 4-column vector. CPL = 8: the lane's columns
+// are contiguous (8 sub .. 8 sub + 7, one 32-byte load per row); otherwise
+// vector v covers columns 4 (sub + v tpn) .. + 3.
+template <int CPL>
+__device__ __forceinline__ int lane_col(int sub, int v, int tpn) {
+  return CPL == 8 ? 8 * sub + 4 * v : 4 * (sub + v * tpn);
+}
+
+// Byte offset of a lane's first column in a factor row.
+template <int CPL, bool BF16>
+__device__ __forceinline__ uint32_t lane_byte_offset(int sub) {
+  return (uint32_t)lane_col<CPL>(sub, 0, 1) * (BF16 ? 2u : 4u);
+}
+
+// Shared-memory flushes: at step k, the lanes of group g add element
+// (k + g) mod 4 of their 4-column vector, so groups flushing in the same
+// instruction use different banks (each group's lanes cover a whole row).
 template <int CPL>
 __device__ __forceinline__ void flush_run(const float (&run)[CPL], uint32_t row, int slot,
-                                          float *temp, float *out, int R, int sub, int tpn) {
+                                          float *temp, float *out, int R, int sub, int tpn,
+                                          int grp) {
   if (slot >= 0) {
     float *t = temp + (size_t)slot * R;
     const int sw = slot_swizzle(slot, R);
+    const int rot = (ALTO_HOT_ROTATE && CPL >= 8) ? (grp & 3) : 0;
 #pragma unroll
     for (int v = 0; v < CPL / 4; ++v) {
-      const int col = (4 * (sub + v * tpn)) ^ sw;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(t + col + k, run[4 * v + k]);
+      const int col = lane_col<CPL>(sub, v, tpn) ^ sw;
+      float e0 = run[4 * v], e1 = run[4 * v + 1], e2 = run[4 * v + 2], e3 = run[4 * v + 3];
+      if (rot & 1) {
+        const float x = e0;
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
+        e3 = x;
+      }
+      if (rot & 2) {
+        const float x = e0, y = e1;
+        e0 = e2;
+        e1 = e3;
+        e2 = x;
+        e3 = y;
+      }
+      atomicAdd(t + col + (rot & 3), e0);
+      atomicAdd(t + col + ((rot + 1) & 3), e1);
+      atomicAdd(t + col + ((rot + 2) & 3), e2);
+      atomicAdd(t + col + ((rot + 3) & 3), e3);
     }
   } else {
     float *o = out + (uint64_t)row * (uint64_t)R;
 #pragma unroll
     for (int v = 0; v < CPL / 4; ++v)
-      red_v4(o + 4 * (sub + v * tpn), run[4 * v], run[4 * v + 1], run[4 * v + 2], run[4 * v + 3]);
+      red_v4(o + lane_col<CPL>(sub, v, tpn), run[4 * v], run[4 * v + 1], run[4 * v + 2], run[4 * v + 3]);
   }
 }
 
@@ -192,6 +232,22 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
       if (k + 1 < N) {
         const char *rb = fb[k] + (uint64_t)ij[k] * rowb;
         float f[CPL];
+        if constexpr (CPL == 8 && !BF16) {
+          asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+              : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]),
+                "=f"(f[7])
+              : "l"(rb));
+        } else if constexpr (CPL == 8) {
+          const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(rb));
+          f[0] = bf16lo(qv.x);
+          f[1] = bf16hi(qv.x);
+          f[2] = bf16lo(qv.y);
+          f[3] = bf16hi(qv.y);
+          f[4] = bf16lo(qv.z);
+          f[5] = bf16hi(qv.z);
+          f[6] = bf16lo(qv.w);
+          f[7] = bf16hi(qv.w);
+        } else {
 #pragma unroll
         for (int w = 0; w < CPL / 4; ++w) {
           const int voff = w * tpn * (BF16 ? 8 : 16);
@@ -209,6 +265,7 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
             f[4 * w + 3] = bf16hi(qv.y);
           }
         }
+        }
 #pragma unroll
         for (int c = 0; c < CPL; ++c) p[c] = (k == 0 ? vj : p[c]) * f[c];
       } else if (k == 0) {
@@ -220,18 +277,26 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] += p[c];
     } else {
-      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn);
+      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn, grp);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] = p[c];
       run_row = rj;
       run_slot = sj;
     }
   }
-  if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn);
+  if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn, grp);
+}
+
+// Wider lanes (8 or 16 columns) keep twice the values in registers: those
+// builds run two CTAs per SM (64 registers) instead of three (40).
+template <int CPL>
+constexpr int mttkrp_min_blocks() {
+  return CPL >= 8 ? 2 : kMttkrpBlocksPerSm;
 }
 
 template <int NT, int KW, int CPL, bool BF16, bool PULL>
-__global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+__global__ void __launch_bounds__(kMttkrpThreads, mttkrp_min_blocks<CPL>())
+    mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
   constexpr int NMAX = NT ? NT : kMaxModes;
   const int N = NT ? NT : a.dp.nmodes;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -243,7 +308,7 @@ __global__ void __launch_bounds__(kMttkrpThreads, kMttkrpBlocksPerSm) mttkrp_ker
   const int ro = a.out_rank;
   // byte offset of this lane's first column vector, and the row strides
   const uint32_t rowb = (uint32_t)R * (BF16 ? 2u : 4u);
-  const uint32_t inb = 4u * (uint32_t)sub * (BF16 ? 2u : 4u);
+  const uint32_t inb = lane_byte_offset<CPL, BF16>(sub);
   constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
   const char *fb[NIN];
 #pragma unroll
