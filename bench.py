@@ -53,6 +53,22 @@ def parse_args():
     return p.parse_args()
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """Slowest rank's time (the job finishes when the last replica does)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(work_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every replica's work over the slowest time."""
+    return world * work_per_rank / (ms_max / 1000.0)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -308,14 +324,9 @@ def run_ours(args):
     barrier()
     launches = alto.alto_kernel_launches() - launches0
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
     work_units = ITERS * N * M * R
-    value = world * work_units / (ms / 1000.0)
+    value = job_value(work_units, world, ms)
 
     # roofline of the dominant kernel (the MTTKRP segment kernel)
     kw = prof.get("_kw", 1)
@@ -467,15 +478,10 @@ def run_e2e(args, alto, coords, vals, spec, A0, world, barrier):
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / steps
     ms = ev0.elapsed_time(ev1) / steps
-    ms = max(ms, wall * 1000.0)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(max(ms, wall * 1000.0), world)
     h2d = coords.nbytes + vals.nbytes + sum(a.nbytes for a in A0)
     d2h = sum(a.nbytes for a in A0) + 8 * R + 8 * ITERS
-    return {"value": world * ITERS * N * M * R / (ms / 1000.0), "unit": UNIT,
+    return {"value": job_value(ITERS * N * M * R, world, ms), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms,
             "steps": steps}
 
