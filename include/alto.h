@@ -320,6 +320,66 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
                       double *fits, double tol, int *iters_done, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * cpapr_run -- CP-APR with multiplicative updates (Alg. 2) for count data:
+ * for each outer iteration and each mode n: S shifts inadmissible zeros
+ * (kappa where A(i,r) < kappa_tol and the previous Phi(i,r) > 1), B = (A^(n)
+ * + S) diag(lambda); then at most l_max times: Phi = (X_(n) ./ max(B Pi,
+ * eps)) Pi^T (the Phi kernel of Alg. 5 on the ALTO tensor, with the MTTKRP's
+ * per-mode conflict resolution), stop when max |min(B, 1 - Phi)| < tau, else
+ * B = B .* Phi; then lambda = e^T B and A^(n) = B diag(lambda)^-1. The whole
+ * run stops after an outer iteration in which no mode took a step.
+ * Pi's rows are recomputed from the factors for every nonzero (OTF) or, for a
+ * mode whose fiber reuse is at most 4 while the other factors are more than
+ * four times the L2 size, precomputed once per mode and outer iteration
+ * (PRE, nnz x R floats; OTF everywhere if that does not fit), Section IV-C.
+ *
+ *  factors  HOST array [nmodes] of pointers to dims[m] x R floats, all device
+ *           or all host: the initial guess (positive) on entry, the
+ *           column-stochastic result on return.
+ *  lambda   [R] double, host or device: the column weights of the result.
+ *  objective  host [k_max] double or NULL: after every outer iteration,
+ *           sum(lambda) - sum over nonzeros of x log M(x) (the negative
+ *           Poisson log-likelihood up to a constant). Costs one sync each.
+ *  inner_steps  host [k_max * nmodes] int or NULL: update steps per outer
+ *           iteration and mode.
+ *  stats    outer iterations run, whether it converged, total update steps,
+ *           modes run with PRE.
+ * Factors and Phi are fp32, lambda and the objective fp64. Synchronises once
+ * per outer iteration. Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * ------------------------------------------------------------------------- */
+/* alto_phi -- the Phi kernel of Alg. 5 alone (a test aid and a building
+ * block): out = (X_(mode) ./ max(B Pi, eps)) Pi^T, i.e. every nonzero adds
+ * v / max(B(i_mode,:) . krp, eps) * krp to row i_mode, krp the Hadamard
+ * product of the other factors' rows. factors: host array [nmodes] of device
+ * I_m x R fp32 matrices (factors[mode] ignored); B: device I_mode x R fp32;
+ * out: device I_mode x R fp32, overwritten. pre != 0 precomputes Pi (nnz x R
+ * floats, allocated and freed on the stream) instead of gathering on the fly.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+alto_status alto_phi(alto_handle_t h, int mode, const float *const *factors, const float *B, int R,
+                     double eps, int pre, float *out, void *stream);
+
+typedef struct alto_apr_params {
+  int k_max;          /* outer iterations (>= 1)                               */
+  int l_max;          /* inner iterations per mode (>= 1); the paper uses 10   */
+  double tau;         /* KKT tolerance (> 0)                                    */
+  double kappa;       /* inadmissible-zero shift (>= 0)                        */
+  double kappa_tol;   /* entries below this may be shifted (>= 0)              */
+  double eps;         /* smallest divisor (> 0)                                 */
+  int variant;        /* 0 = PRE/OTF per mode by the rule above, 1 = OTF, 2 = PRE */
+} alto_apr_params;
+
+typedef struct alto_apr_stats {
+  int outer_done;
+  int converged;
+  int inner_steps_total;
+  int pre_modes;
+} alto_apr_stats;
+
+alto_status cpapr_run(alto_handle_t h, int R, const alto_apr_params *params, float *const *factors,
+                      double *lambda, double *objective, int *inner_steps, alto_apr_stats *stats,
+                      void *stream);
+
+/* ---------------------------------------------------------------------------
  * CP-ALS batch -- many CP-ALS runs (Alg. 1) on different tensors advanced
  * together on one stream: a step performs one mode update of every active run
  * (prepare, grouped MTTKRP, update, finish: the same arithmetic as cpals_run),

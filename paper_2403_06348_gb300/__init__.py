@@ -78,6 +78,20 @@ class alto_tune_result(ctypes.Structure):
 ALTO_TUNE_SEGMENTS = 1
 
 
+class alto_apr_params(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int), ("l_max", ctypes.c_int), ("tau", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("kappa_tol", ctypes.c_double), ("eps", ctypes.c_double),
+                ("variant", ctypes.c_int)]
+
+
+class alto_apr_stats(ctypes.Structure):
+    _fields_ = [("outer_done", ctypes.c_int), ("converged", ctypes.c_int),
+                ("inner_steps_total", ctypes.c_int), ("pre_modes", ctypes.c_int)]
+
+
+APR_AUTO, APR_OTF, APR_PRE = 0, 1, 2
+
+
 class alto_batch_info(ctypes.Structure):
     _fields_ = [("active", ctypes.c_int), ("slots_span", ctypes.c_int), ("steps", ctypes.c_uint64),
                 ("graph_launches", ctypes.c_uint64), ("bytes_held", ctypes.c_uint64),
@@ -115,6 +129,9 @@ SIGNATURES = {
     "alto_cpals_footprint": ([_i32, _vp, _u64, _i32, _i32, ctypes.POINTER(_u64),
                               ctypes.POINTER(_u64)], _i32),
     "alto_fill_uniform": ([_vp, _u64, _u64, _vp], _i32),
+    "alto_phi": ([_vp, _i32, _vp, _vp, _i32, ctypes.c_double, _i32, _vp, _vp], _i32),
+    "cpapr_run": ([_vp, _i32, ctypes.POINTER(alto_apr_params), _vp, _vp, _vp, _vp,
+                   ctypes.POINTER(alto_apr_stats), _vp], _i32),
     "alto_autotune": ([_vp, _i32, _vp, _i32, _vp, _i32, _vp, ctypes.POINTER(alto_tune_result)], _i32),
     "alto_profile_enable": ([_vp, _i32], _i32),
     "alto_profile_read": ([_vp, ctypes.POINTER(alto_profile), _i32], _i32),
@@ -465,6 +482,38 @@ class AltoTensor:
                 "ms": [float(res.ms[i]) for i in range(n)],
                 "default_ms": [float(res.default_ms[i]) for i in range(n)],
                 "nparts": int(res.nparts), "candidates": int(res.candidates)}
+
+    def phi(self, mode: int, factors, B, R: int, eps: float = 1e-10, pre: bool = False, out=None,
+            stream=None):
+        """alto_phi: the CP-APR model update Phi of Alg. 5 for one mode."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.dims[mode], R), dtype=torch.float32, device="cuda")
+        arr = (ctypes.c_void_p * self.nmodes)(*[_ptr(f) for f in factors])
+        _check(lib().alto_phi(self.handle, int(mode), arr, _ptr(B), int(R), float(eps),
+                              1 if pre else 0, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def cpapr(self, R: int, factors, k_max: int, l_max: int = 10, tau: float = 1e-4,
+              kappa: float = 1e-2, kappa_tol: float = 1e-10, eps: float = 1e-10,
+              variant: int = APR_AUTO, stream=None) -> dict:
+        """cpapr_run in place on ``factors`` (CUDA float32 tensors or numpy
+        float32 arrays). Returns lambda, objectives, inner steps and stats."""
+        torch = _torch()
+        on_dev = not isinstance(factors[0], np.ndarray)
+        lam = torch.empty(R, dtype=torch.float64, device="cuda") if on_dev else np.empty(R)
+        obj = np.zeros(k_max)
+        steps = np.zeros((k_max, self.nmodes), dtype=np.int32)
+        prm = alto_apr_params(int(k_max), int(l_max), float(tau), float(kappa), float(kappa_tol),
+                              float(eps), int(variant))
+        st = alto_apr_stats()
+        arr = (ctypes.c_void_p * self.nmodes)(*[_ptr(f) for f in factors])
+        _check(lib().cpapr_run(self.handle, int(R), ctypes.byref(prm), arr, _ptr(lam), obj.ctypes.data,
+                               steps.ctypes.data, ctypes.byref(st), _stream_ptr(stream)))
+        k = int(st.outer_done)
+        return {"lam": lam.cpu().numpy() if on_dev else lam, "objective": obj[:k].tolist(),
+                "inner": steps[:k].tolist(), "outer_done": k, "converged": bool(st.converged),
+                "inner_steps_total": int(st.inner_steps_total), "pre_modes": int(st.pre_modes)}
 
     def cpals(self, R: int, iters: int, factors, tol: float = 0.0, stream=None):
         """Run CP-ALS in place on ``factors`` (CUDA float32 tensors or numpy

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "alto_internal.cuh"
+#include "apr.cuh"
 #include "cpals.cuh"
 #include "handle.cuh"
 #include "encode.cuh"
@@ -527,6 +528,77 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
 }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Phi^(n) of Alg. 5 into phi (which the ATOMIC variant needs zeroed; the
+// caller's inner_begin kernel does that) with the same per-mode conflict
+// resolution as the MTTKRP: hot rows staged (ATOMIC) or segment Temp and the
+// pull reduction (PULL). 4 fp32 columns per lane.
+alto_status phi_impl(alto_tensor *h, int mode, const float *const *A, const float *B,
+                     const float *pimat, float eps, int R, float *phi, const int *skip,
+                     cudaStream_t s) {
+  alto_mode_plan p;
+  alto_status st = resolve_plan(h, mode, R, &p);
+  if (st != ALTO_OK) return st;
+  MttkrpArgs a{};
+  a.bp = h->bp;
+  a.bp.out_rank = h->rank_of[mode];
+  a.out_rank = h->rank_of[mode];
+  a.dp.nmodes = h->N;
+  a.dp.kw = h->kw;
+  for (int q = 0; q < h->N; ++q) {
+    const int m = h->mode_of[q];
+    a.dp.nruns[q] = h->dp32.nruns[m];
+    memcpy(a.dp.runs[q], h->dp32.runs[m], sizeof(a.dp.runs[q]));
+    a.factors[q] = m == mode ? nullptr : A[m];
+  }
+  for (int q = 0, k = 0; q < h->N; ++q)
+    if (h->mode_of[q] != mode) a.fin[k++] = A[h->mode_of[q]];
+  a.keys = h->keys;
+  a.vals = h->vals;
+  a.nnz = h->M;
+  a.L = h->L;
+  a.intervals = h->intervals;
+  a.out = phi;
+  a.mode = mode;
+  a.R = R;
+  a.bmat = B;
+  a.pimat = pimat;
+  a.eps = eps;
+  a.skip = skip;
+  {
+    const uint64_t per_seg = std::max<uint64_t>(h->M / std::max<uint64_t>(h->L, 1), 1);
+    a.flush_every = (int)std::max<uint64_t>(1, 32768 / per_seg);
+  }
+  if (h->M == 0) return ALTO_OK;
+  const bool pre = pimat != nullptr;
+  if (p.variant == ALTO_VARIANT_PULL) {
+    if ((st = ensure_pull(h, mode, s)) != ALTO_OK) return st;
+    const PullPlan &pp = h->pull[mode];
+    const size_t need = pp.total_rows * (size_t)R * sizeof(float);
+    if (h->partials.bytes < need) {
+      dfree(h, h->partials.p, h->partials.bytes, s);
+      h->partials.p = dalloc(h, need, s);
+      h->partials.bytes = h->partials.p ? need : 0;
+      if (!h->partials.p) return fail(ALTO_ERR_OOM, "pull partials of %zu bytes", need);
+    }
+    a.partials = static_cast<float *>(h->partials.p);
+    a.part_off = pp.part_off;
+    const size_t smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
+    CUDA_TRY(launch_phi(a, true, pre, smem, h->num_sms, s));
+    CUDA_TRY(launch_pull_reduce(a.partials, pp.row_ptr, pp.prow, h->dims[mode], R, phi, h->num_sms,
+                                s, skip));
+  } else {
+    if ((st = ensure_hot_table(h, mode, p.hot_rows, s)) != ALTO_OK) return st;
+    const HotTable &ht = h->hot_tab[mode];
+    a.htab = ht.htab;
+    a.slot_rows = h->hot_rows[mode];
+    a.hbits = ht.hbits;
+    a.nslots = ht.nslots;
+    const size_t smem = mttkrp_smem_bytes(false, R, ht.nslots, ht.hbits, 0);
+    CUDA_TRY(launch_phi(a, false, pre, smem, h->num_sms, s));
+  }
+  return ALTO_OK;
+}
 
 }  // namespace
 
@@ -1221,6 +1293,235 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
   res->nparts = best_L;
   res->candidates = timed;
   return done(ALTO_OK);
+}
+
+alto_status cpapr_run(alto_handle_t h, int R, const alto_apr_params *prm, float *const *factors,
+                      double *lambda, double *objective, int *inner_steps, alto_apr_stats *stats,
+                      void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  if (!prm || !factors || !lambda) return fail(ALTO_ERR_INVALID_ARG, "params/factors/lambda NULL");
+  if (prm->k_max < 1 || prm->l_max < 1) return fail(ALTO_ERR_INVALID_ARG, "k_max and l_max must be >= 1");
+  if (!(prm->tau > 0.0) || !(prm->kappa >= 0.0) || !(prm->kappa_tol >= 0.0) || !(prm->eps > 0.0))
+    return fail(ALTO_ERR_INVALID_ARG, "tau and eps must be > 0, kappa and kappa_tol >= 0");
+  if (prm->variant < 0 || prm->variant > 2) return fail(ALTO_ERR_INVALID_ARG, "variant %d", prm->variant);
+  if (h->M == 0) return fail(ALTO_ERR_INVALID_ARG, "CP-APR needs nnz > 0");
+  const int N = h->N;
+  int ndev = 0;
+  for (int m = 0; m < N; ++m) {
+    if (!factors[m]) return fail(ALTO_ERR_INVALID_ARG, "factors[%d] is NULL", m);
+    if (!aligned16(factors[m])) return fail(ALTO_ERR_INVALID_ARG, "factors[%d] not 16-byte aligned", m);
+    ndev += is_device_ptr(factors[m]) ? 1 : 0;
+  }
+  if (ndev != 0 && ndev != N) return fail(ALTO_ERR_INVALID_ARG, "factors mix host and device memory");
+  const bool host_factors = ndev == 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  const int K = prm->k_max;
+  uint64_t maxI = 0, sumI = 0;
+  for (int m = 0; m < N; ++m) {
+    maxI = std::max(maxI, h->dims[m]);
+    sumI += h->dims[m];
+  }
+  // PRE (precomputed Pi) or OTF per mode, Section IV-C: precompute where the
+  // mode's fiber reuse is limited and the other factors are much larger than
+  // the fast memory (the L2 here); otherwise recompute on the fly.
+  bool pre[kMaxModes] = {};
+  bool any_pre = false;
+  {
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    for (int n = 0; n < N; ++n) {
+      const double reuse = (double)h->M / (double)std::max<uint64_t>(h->dims[n], 1);
+      const uint64_t others = (sumI - h->dims[n]) * (uint64_t)R * 4;
+      pre[n] = prm->variant == 2 || (prm->variant == 0 && reuse <= 4.0 && others > 4ull * (uint64_t)l2);
+      any_pre |= pre[n];
+    }
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_A = take(host_factors ? sumI * R * 4 : 0), o_B = take(maxI * R * 4),
+               o_phi = take(sumI * R * 4), o_lam = take((size_t)R * 8), o_sum = take((size_t)R * 8),
+               o_acc = take(8), o_flags = take(16), o_steps = take((size_t)K * N * 4);
+  size_t o_pi = any_pre ? take(h->M * (uint64_t)R * 4) : 0;
+  char *ws = static_cast<char *>(dalloc(h, off, s));
+  if (!ws && any_pre) {  // Pi does not fit: recompute on the fly everywhere
+    off = o_pi;
+    any_pre = false;
+    for (int n = 0; n < N; ++n) pre[n] = false;
+    ws = static_cast<char *>(dalloc(h, off, s));
+  }
+  if (!ws) return fail(ALTO_ERR_OOM, "CP-APR workspace of %zu bytes", off);
+  float *A[kMaxModes], *Phi[kMaxModes];
+  {
+    size_t fo = o_A, po = o_phi;
+    for (int m = 0; m < N; ++m) {
+      A[m] = host_factors ? reinterpret_cast<float *>(ws + fo) : factors[m];
+      Phi[m] = reinterpret_cast<float *>(ws + po);
+      fo += h->dims[m] * R * 4;
+      po += h->dims[m] * R * 4;
+    }
+  }
+  float *B = reinterpret_cast<float *>(ws + o_B);
+  double *lam = reinterpret_cast<double *>(ws + o_lam);
+  double *sums = reinterpret_cast<double *>(ws + o_sum);
+  double *acc = reinterpret_cast<double *>(ws + o_acc);
+  int *done = reinterpret_cast<int *>(ws + o_flags);
+  int *stepped = done + 1;
+  unsigned *kkt = reinterpret_cast<unsigned *>(done + 2);
+  int *steps = reinterpret_cast<int *>(ws + o_steps);
+  float *pim = any_pre ? reinterpret_cast<float *>(ws + o_pi) : nullptr;
+  auto finish = [&](alto_status code) {
+    dfree(h, ws, off, s);
+    return code;
+  };
+#define AP_TRY(expr)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return finish(fail(ALTO_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_))); \
+  } while (0)
+#define AP_ST(expr)                                \
+  do {                                             \
+    alto_status s_ = (expr);                       \
+    if (s_ != ALTO_OK) return finish(s_);          \
+  } while (0)
+  if (host_factors)
+    for (int m = 0; m < N; ++m)
+      AP_TRY(cudaMemcpyAsync(A[m], factors[m], h->dims[m] * R * 4, cudaMemcpyHostToDevice, s));
+  {
+    std::vector<double> ones((size_t)R, 1.0);
+    AP_TRY(cudaMemcpyAsync(lam, ones.data(), (size_t)R * 8, cudaMemcpyHostToDevice, s));
+  }
+  AP_TRY(cudaMemsetAsync(steps, 0, (size_t)K * N * 4, s));
+  AP_TRY(cudaMemsetAsync(ws + o_phi, 0, sumI * R * 4, s));
+  // the initial guess as column-stochastic factors and lambda (same model)
+  for (int m = 0; m < N; ++m) {
+    AP_TRY(cudaMemsetAsync(sums, 0, (size_t)R * 8, s));
+    AP_TRY(launch_colsum(A[m], h->dims[m], R, sums, h->num_sms, s));
+    AP_TRY(launch_normalize(A[m], h->dims[m], R, sums, lam, h->num_sms, s));
+  }
+  FactorPtrs fp{};
+  const float *Ac[kMaxModes];
+  for (int m = 0; m < N; ++m) {
+    fp.p[m] = A[m];
+    Ac[m] = A[m];
+  }
+  const float eps = (float)prm->eps, tau = (float)prm->tau;
+  const float kappa = (float)prm->kappa, kappa_tol = (float)prm->kappa_tol;
+  int outer_done = 0;
+  bool converged = false;
+  std::vector<double> lam_h((size_t)R);
+  for (int k = 0; k < K; ++k) {
+    AP_TRY(cudaMemsetAsync(stepped, 0, sizeof(int), s));
+    for (int n = 0; n < N; ++n) {
+      const uint64_t I = h->dims[n];
+      alto_mode_plan p;
+      AP_ST(resolve_plan(h, n, R, &p));
+      AP_TRY(launch_shift_scale(A[n], Phi[n], I, R, lam, k > 0 ? 1 : 0, kappa, kappa_tol, B,
+                                h->num_sms, s));
+      if (pre[n]) AP_TRY(launch_pi(h->dp, h->keys, h->M, n, fp, R, pim, h->num_sms, s));
+      AP_TRY(cudaMemsetAsync(done, 0, sizeof(int), s));
+      for (int l = 0; l < prm->l_max; ++l) {
+        AP_TRY(launch_inner_begin(Phi[n], I, R, p.variant != ALTO_VARIANT_PULL, kkt, done,
+                                  h->num_sms, s));
+        {
+          ProfScope ps(h, ALTO_PROF_MTTKRP, s);
+          AP_ST(phi_impl(h, n, Ac, B, pre[n] ? pim : nullptr, eps, R, Phi[n], done, s));
+        }
+        AP_TRY(launch_kkt(B, Phi[n], I, R, kkt, done, h->num_sms, s));
+        AP_TRY(launch_mu(B, Phi[n], I, R, kkt, tau, done, stepped, steps + k * N + n, h->num_sms, s));
+      }
+      // lambda = e^T B, A^(n) = B diag(lambda)^-1
+      AP_TRY(cudaMemsetAsync(sums, 0, (size_t)R * 8, s));
+      AP_TRY(launch_colsum(B, I, R, sums, h->num_sms, s));
+      AP_TRY(cudaMemcpyAsync(A[n], B, I * R * 4, cudaMemcpyDeviceToDevice, s));
+      AP_TRY(launch_normalize(A[n], I, R, sums, nullptr, h->num_sms, s));
+      AP_TRY(cudaMemcpyAsync(lam, sums, (size_t)R * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    outer_done = k + 1;
+    if (objective) {
+      AP_TRY(cudaMemsetAsync(acc, 0, 8, s));
+      AP_TRY(launch_loglik(h->dp, h->keys, h->vals, h->M, fp, lam, R, acc, h->num_sms, s));
+      double ll = 0.0;
+      AP_TRY(cudaMemcpyAsync(&ll, acc, 8, cudaMemcpyDeviceToHost, s));
+      AP_TRY(cudaMemcpyAsync(lam_h.data(), lam, (size_t)R * 8, cudaMemcpyDeviceToHost, s));
+      AP_TRY(cudaStreamSynchronize(s));
+      double total = 0.0;
+      for (int r = 0; r < R; ++r) total += lam_h[r];
+      objective[k] = total - ll;
+    }
+    int stp = 1;
+    AP_TRY(cudaMemcpyAsync(&stp, stepped, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AP_TRY(cudaStreamSynchronize(s));
+    if (stp == 0) {
+      converged = true;
+      break;
+    }
+  }
+  if (host_factors)
+    for (int m = 0; m < N; ++m)
+      AP_TRY(cudaMemcpyAsync(factors[m], A[m], h->dims[m] * R * 4, cudaMemcpyDeviceToHost, s));
+  AP_TRY(cudaMemcpyAsync(lambda, lam, (size_t)R * 8, cudaMemcpyDefault, s));
+  std::vector<int> st_h((size_t)K * N);
+  AP_TRY(cudaMemcpyAsync(st_h.data(), steps, (size_t)K * N * 4, cudaMemcpyDeviceToHost, s));
+  AP_TRY(cudaStreamSynchronize(s));
+  if (inner_steps) memcpy(inner_steps, st_h.data(), (size_t)K * N * 4);
+  if (stats) {
+    stats->outer_done = outer_done;
+    stats->converged = converged ? 1 : 0;
+    int tot = 0;
+    for (int v : st_h) tot += v;
+    stats->inner_steps_total = tot;
+    int npre = 0;
+    for (int n = 0; n < N; ++n) npre += pre[n] ? 1 : 0;
+    stats->pre_modes = npre;
+  }
+#undef AP_TRY
+#undef AP_ST
+  return finish(ALTO_OK);
+}
+
+alto_status alto_phi(alto_handle_t h, int mode, const float *const *factors, const float *B, int R,
+                     double eps, int pre, float *out, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < 0 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "mode %d out of range", mode);
+  if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  if (!factors || !B || !out) return fail(ALTO_ERR_INVALID_ARG, "factors/B/out NULL");
+  if (!(eps > 0.0)) return fail(ALTO_ERR_INVALID_ARG, "eps must be > 0");
+  if (!aligned16(B) || !aligned16(out)) return fail(ALTO_ERR_INVALID_ARG, "B/out not 16-byte aligned");
+  for (int m = 0; m < h->N; ++m) {
+    if (m == mode) continue;
+    if (!factors[m] || !aligned16(factors[m]))
+      return fail(ALTO_ERR_INVALID_ARG, "factors[%d] NULL or not 16-byte aligned", m);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  const uint64_t I = h->dims[mode];
+  CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
+  if (h->M == 0) return ALTO_OK;
+  float *pim = nullptr;
+  const size_t pbytes = h->M * (size_t)R * sizeof(float);
+  if (pre) {
+    pim = static_cast<float *>(dalloc(h, pbytes, s));
+    if (!pim) return fail(ALTO_ERR_OOM, "Pi of %zu bytes", pbytes);
+    FactorPtrs fp{};
+    for (int m = 0; m < h->N; ++m) fp.p[m] = m == mode ? nullptr : factors[m];
+    cudaError_t e = launch_pi(h->dp, h->keys, h->M, mode, fp, R, pim, h->num_sms, s);
+    if (e != cudaSuccess) {
+      dfree(h, pim, pbytes, s);
+      return fail(ALTO_ERR_CUDA, "Pi: %s", cudaGetErrorString(e));
+    }
+  }
+  st = phi_impl(h, mode, factors, B, pim, (float)eps, R, out, nullptr, s);
+  if (pim) dfree(h, pim, pbytes, s);
+  return st;
 }
 
 }  // extern "C"

@@ -10,7 +10,9 @@ namespace alto {
 __global__ void __launch_bounds__(256) pull_reduce_kernel(const float *__restrict__ partials,
                                                           const uint64_t *__restrict__ row_ptr,
                                                           const uint64_t *__restrict__ prow,
-                                                          uint64_t I, int R, float *__restrict__ out) {
+                                                          uint64_t I, int R, float *__restrict__ out,
+                                                          const int *__restrict__ skip) {
+  if (skip && *skip) return;
   const int per_row = R / 4;
   const uint64_t total = I * (uint64_t)per_row;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -68,14 +70,26 @@ cudaError_t launch_mttkrp(const MttkrpArgs &a, int cpl, bool bf16, bool pull, si
 }
 
 cudaError_t launch_pull_reduce(const float *partials, const uint64_t *row_ptr, const uint64_t *prow,
-                               uint64_t I, int R, float *out, int num_sms, cudaStream_t s) {
+                               uint64_t I, int R, float *out, int num_sms, cudaStream_t s,
+                               const int *skip) {
   const uint64_t total = I * (uint64_t)(R / 4);
   uint64_t grid = (total + 255) / 256;
   if (grid > (uint64_t)num_sms * 16) grid = (uint64_t)num_sms * 16;
   if (grid < 1) grid = 1;
-  pull_reduce_kernel<<<(unsigned)grid, 256, 0, s>>>(partials, row_ptr, prow, I, R, out);
+  pull_reduce_kernel<<<(unsigned)grid, 256, 0, s>>>(partials, row_ptr, prow, I, R, out, skip);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_phi(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
+                       cudaStream_t s) {
+  if (a.nnz == 0) return cudaSuccess;
+  switch (a.dp.nmodes) {
+    case 3: return launch_phi_nt<3>(a, pull, pre, smem, num_sms, s);
+    case 4: return launch_phi_nt<4>(a, pull, pre, smem, num_sms, s);
+    case 5: return launch_phi_nt<5>(a, pull, pre, smem, num_sms, s);
+    default: return launch_phi_nt<0>(a, pull, pre, smem, num_sms, s);
+  }
 }
 
 }  // namespace alto

@@ -41,6 +41,11 @@ struct MttkrpArgs {
   // PULL variant
   float *partials;             // Temp_l of every segment, back to back
   const uint64_t *part_off;    // first partial row of each segment [L]
+  // CP-APR model update Phi (Alg. 5)
+  const float *bmat;           // B of the output mode [I_n][R]
+  const float *pimat;          // precomputed Pi [nnz][R] (PRE) or null (OTF)
+  float eps;
+  const int *skip;             // nonzero: return at once (inner loop converged)
 };
 
 // Shared memory the segment kernel needs.
@@ -62,6 +67,15 @@ cudaError_t launch_mttkrp_nt(const MttkrpArgs &a, int cpl, bool bf16, bool pull,
                              int num_sms, cudaStream_t s);
 
 cudaError_t launch_pull_reduce(const float *partials, const uint64_t *row_ptr, const uint64_t *prow,
-                               uint64_t I, int R, float *out, int num_sms, cudaStream_t s);
+                               uint64_t I, int R, float *out, int num_sms, cudaStream_t s,
+                               const int *skip = nullptr);
+
+// Phi (Alg. 5) for a.mode: a.bmat set, a.pimat set for PRE.
+cudaError_t launch_phi(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
+                       cudaStream_t s);
+
+template <int NT>
+cudaError_t launch_phi_nt(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
+                          cudaStream_t s);
 
 }  // namespace alto

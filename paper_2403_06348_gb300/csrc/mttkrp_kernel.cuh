@@ -203,12 +203,27 @@ __device__ __forceinline__ void decode_blocks(const BlockPlan &bp, uint64_t lo, 
 // column vectors sub, sub + tpn, ...), multiplies, and sums runs of equal
 // output row in registers before flushing them. TAIL batches check j < nvalid.
 // fb[k] is the k-th input factor plus this lane's byte offset (inb).
-template <int NMAX, int CPL, bool BF16, bool TAIL>
+//
+// APR != 0 computes the CP-APR model update Phi (Alg. 5) instead: the group's
+// Khatri-Rao row krp (the product of the gathered rows, or row pos0 + j of the
+// precomputed Pi when APR == kAprPre) is dotted with row rj of B over the
+// group's lanes, and the run receives v / max(B(rj,:) . krp, eps) * krp.
+constexpr int kAprOff = 0, kAprOtf = 1, kAprPre = 2;
+
+struct AprArgs {
+  const float *bmat;   // B of the output mode [I_n][R]
+  const float *pimat;  // Pi [nnz][R] in ALTO order (kAprPre)
+  float eps;
+  uint64_t pos0;       // ordered position of the batch's first nonzero
+};
+
+template <int NMAX, int CPL, bool BF16, bool TAIL, int APR = kAprOff>
 __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? NMAX - 1 : 1],
                                              float *out, int R, int N, int tpn, int grp, int sub,
                                              float v, int slot, uint32_t row,
                                              const uint32_t (&in)[NMAX > 1 ? NMAX - 1 : 1], int nvalid,
-                                             float *temp, uint32_t rowb) {
+                                             float *temp, uint32_t rowb, const AprArgs &apr = AprArgs{}) {
+  static_assert(APR == kAprOff || (CPL == 4 && !BF16), "Phi uses 4 fp32 columns per lane");
   constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
   const unsigned full = 0xffffffffu;
   float run[CPL];
@@ -224,9 +239,42 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
     const uint32_t rj = __shfl_sync(full, row, j);
     uint32_t ij[NIN];
 #pragma unroll
-    for (int k = 0; k < NIN; ++k) ij[k] = (k + 1 < N) ? __shfl_sync(full, in[k], j) : 0u;
-    if (TAIL && j >= nvalid) continue;
+    for (int k = 0; k < NIN; ++k)
+      ij[k] = (APR != kAprPre && k + 1 < N) ? __shfl_sync(full, in[k], j) : 0u;
     float p[CPL];
+    if constexpr (APR != kAprOff) {
+      const bool live = !TAIL || j < nvalid;
+      float kr[4] = {1.f, 1.f, 1.f, 1.f};
+      if (APR == kAprPre) {
+        if (live) {
+          const float4 qv = __ldg(reinterpret_cast<const float4 *>(apr.pimat) +
+                                  (apr.pos0 + (uint64_t)j) * (uint64_t)(R / 4) + sub);
+          kr[0] = qv.x;
+          kr[1] = qv.y;
+          kr[2] = qv.z;
+          kr[3] = qv.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) {
+          if (k + 1 < N) {
+            const float4 qv = __ldg(reinterpret_cast<const float4 *>(fb[k] + (uint64_t)ij[k] * rowb));
+            kr[0] *= qv.x;
+            kr[1] *= qv.y;
+            kr[2] *= qv.z;
+            kr[3] *= qv.w;
+          }
+        }
+      }
+      const float4 bv = __ldg(reinterpret_cast<const float4 *>(apr.bmat) + (uint64_t)rj * (R / 4) + sub);
+      float dot = kr[0] * bv.x + kr[1] * bv.y + kr[2] * bv.z + kr[3] * bv.w;
+      for (int o = 1; o < tpn; o <<= 1) dot += __shfl_xor_sync(full, dot, o);
+      if (!live) continue;
+      const float scale = vj / fmaxf(dot, apr.eps);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p[c] = scale * kr[c];
+    } else {
+    if (TAIL && j >= nvalid) continue;
 #pragma unroll
     for (int k = 0; k < NIN; ++k) {
       if (k + 1 < N) {
@@ -273,6 +321,7 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
         for (int c = 0; c < CPL; ++c) p[c] = vj;
       }
     }
+    }
     if (ALTO_MTTKRP_RUNS && rj == run_row) {
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] += p[c];
@@ -294,9 +343,10 @@ constexpr int mttkrp_min_blocks() {
   return CPL >= 8 ? 2 : kMttkrpBlocksPerSm;
 }
 
-template <int NT, int KW, int CPL, bool BF16, bool PULL>
+template <int NT, int KW, int CPL, bool BF16, bool PULL, int APR = kAprOff>
 __global__ void __launch_bounds__(kMttkrpThreads, mttkrp_min_blocks<CPL>())
     mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+  if (APR != kAprOff && a.skip && *a.skip) return;  // CP-APR inner loop already converged
   constexpr int NMAX = NT ? NT : kMaxModes;
   const int N = NT ? NT : a.dp.nmodes;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -373,12 +423,14 @@ __global__ void __launch_bounds__(kMttkrpThreads, mttkrp_min_blocks<CPL>())
       int slot = -1;
       if (valid) slot = PULL ? (int)(row - Ts) : hot_lookup(htab, a.hbits, row);
       const uint64_t rem = s1 - base;
+      AprArgs apr{};
+      if constexpr (APR != kAprOff) apr = AprArgs{a.bmat, a.pimat, a.eps, base};
       if (rem >= 32)
-        group_rounds<NMAX, CPL, BF16, false>(fb, a.out, R, N, tpn, grp, sub, v, slot, row, in, 32,
-                                             temp, rowb);
+        group_rounds<NMAX, CPL, BF16, false, APR>(fb, a.out, R, N, tpn, grp, sub, v, slot, row, in,
+                                                  32, temp, rowb, apr);
       else
-        group_rounds<NMAX, CPL, BF16, true>(fb, a.out, R, N, tpn, grp, sub, v, slot, row, in,
-                                            (int)rem, temp, rowb);
+        group_rounds<NMAX, CPL, BF16, true, APR>(fb, a.out, R, N, tpn, grp, sub, v, slot, row, in,
+                                                 (int)rem, temp, rowb, apr);
     }
     if (PULL) {
       __syncthreads();
@@ -612,6 +664,42 @@ static cudaError_t launch_kc(const MttkrpArgs &a, bool bf16, bool pull, size_t s
                 : launch_one<NT, KW, CPL, true, false>(a, smem, num_sms, s);
   return pull ? launch_one<NT, KW, CPL, false, true>(a, smem, num_sms, s)
               : launch_one<NT, KW, CPL, false, false>(a, smem, num_sms, s);
+}
+
+// The CP-APR model update Phi (Alg. 5) through the same kernel: 4 fp32
+// columns per lane, ATOMIC (hot rows staged) or PULL, the Khatri-Rao rows
+// gathered on the fly (OTF) or read from a precomputed Pi (PRE).
+template <int NT, int KW, bool PULL, int APR>
+static cudaError_t launch_phi_one(const MttkrpArgs &a, size_t smem, int num_sms, cudaStream_t s) {
+  auto kern = mttkrp_kernel<NT, KW, 4, false, PULL, APR>;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mttkrp_smem_limit());
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
+  uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, smem);
+  if (grid > a.L) grid = a.L;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, kMttkrpThreads, smem, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_phi_nt(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
+                          cudaStream_t s) {
+  if (a.dp.kw == 1) {
+    if (pull) return pre ? launch_phi_one<NT, 1, true, kAprPre>(a, smem, num_sms, s)
+                         : launch_phi_one<NT, 1, true, kAprOtf>(a, smem, num_sms, s);
+    return pre ? launch_phi_one<NT, 1, false, kAprPre>(a, smem, num_sms, s)
+               : launch_phi_one<NT, 1, false, kAprOtf>(a, smem, num_sms, s);
+  }
+  if (pull) return pre ? launch_phi_one<NT, 2, true, kAprPre>(a, smem, num_sms, s)
+                       : launch_phi_one<NT, 2, true, kAprOtf>(a, smem, num_sms, s);
+  return pre ? launch_phi_one<NT, 2, false, kAprPre>(a, smem, num_sms, s)
+             : launch_phi_one<NT, 2, false, kAprOtf>(a, smem, num_sms, s);
 }
 
 template <int NT>
