@@ -22,7 +22,9 @@ Readings of the paper that this file fixes (each also listed in the design doc):
   empty segment gets the empty interval (2^32-1, 0) in every mode.
 * CP-ALS (Alg. 1): the pseudo-inverse is taken through a Cholesky solve when V
   is positive definite, else numpy's pinv; "column normalize" uses 2-norms
-  every iteration, a zero column gets lambda 0 and stays unscaled; the fit is
+  every iteration, a zero column (norm at most 1e-12 of the largest column's,
+  i.e. rounding noise of a pseudo-inverse solve) gets lambda 0 and is set to
+  zero; the fit is
   1 - ||X - X_hat|| / ||X|| evaluated with the usual expansion
   ||X||^2 + lambda^T (*_m G_m) lambda - 2 <X, X_hat>.
 * Duplicate coordinates are separate COO entries that add up into one cell of
@@ -336,6 +338,10 @@ def cp_fit(normX2: float, lam: np.ndarray, factors: Sequence[np.ndarray],
     return 1.0 - np.sqrt(resid2) / np.sqrt(normX2)
 
 
+# Relative norm under which a column of an update counts as zero.
+ZERO_COLUMN_REL = 1e-12
+
+
 def cp_als_mode_update(coords: np.ndarray, vals: np.ndarray, A: List[np.ndarray], n: int,
                        mttkrp_fn=None) -> Tuple[np.ndarray, np.ndarray]:
     """One pass of the inner loop of Alg. 1 for mode n, updating A[n] in place:
@@ -352,7 +358,10 @@ def cp_als_mode_update(coords: np.ndarray, vals: np.ndarray, A: List[np.ndarray]
     M = mttkrp_fn(coords, vals, A, n)
     An = _solve_spd_or_pinv(V, M)
     lam = np.sqrt(np.sum(An * An, axis=0))
-    scale = np.where(lam > 0, 1.0 / np.where(lam > 0, lam, 1.0), 1.0)
+    # a column of rounding noise (norm below 1e-12 of the largest) is a zero
+    # column: lambda_r = 0 and the column is set to 0, not scaled up
+    lam = np.where(lam > ZERO_COLUMN_REL * np.max(lam, initial=0.0), lam, 0.0)
+    scale = np.where(lam > 0, 1.0 / np.where(lam > 0, lam, 1.0), 0.0)
     A[n] = An * scale
     return M, lam
 
