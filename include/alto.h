@@ -43,7 +43,7 @@ typedef enum alto_status {
   ALTO_ERR_CUDA = -3,          /* a CUDA runtime call failed                    */
   ALTO_ERR_UNSUPPORTED = -4,   /* > 128 index bits, rank not in {4,8,16,32,64}  */
   ALTO_ERR_COORD_RANGE = -5,   /* a coordinate >= dims[n] (detected on device)  */
-  ALTO_ERR_NOT_SPD = -6,       /* CP-ALS: V of Alg. 1 not positive definite     */
+  ALTO_ERR_NOT_SPD = -6,       /* CP-ALS: V of Alg. 1 not usable (non-finite)   */
   ALTO_ERR_TIMEOUT = -7        /* a bounded device wait gave up                 */
 } alto_status;
 
@@ -313,8 +313,11 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
  *  iters_done  host int, iterations run, or NULL.
  * Synchronises when fits, iters_done or host factors are given, and always
  * reads back the device status at the end. Requires nnz > 0.
- * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, NOT_SPD (V not positive
- * definite: the factors are left at the last completed update).
+ * A V that is not positive definite (the Cholesky factorisation meets a pivot
+ * <= 0) is inverted through its eigendecomposition instead (fp64 Jacobi,
+ * eigenvalues below 1e-15 of the largest dropped): the pseudo-inverse Alg. 1
+ * names. Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA, NOT_SPD (V has a
+ * non-finite entry: the factors are left at the last completed update).
  * ------------------------------------------------------------------------- */
 alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, double *lambda,
                       double *fits, double tol, int *iters_done, void *stream);
@@ -429,6 +432,7 @@ typedef struct alto_batch_info {
   uint64_t graph_launches;   /* graph launches enqueued                          */
   uint64_t bytes_held;       /* device bytes held by the batch                   */
   int pending_readbacks;
+  double gpu_ms;             /* device time of the finished steps (CUDA events)  */
 } alto_batch_info;
 
 alto_status alto_batch_create(int max_slots, const alto_allocator *alloc, void *stream,

@@ -95,7 +95,7 @@ APR_AUTO, APR_OTF, APR_PRE = 0, 1, 2
 class alto_batch_info(ctypes.Structure):
     _fields_ = [("active", ctypes.c_int), ("slots_span", ctypes.c_int), ("steps", ctypes.c_uint64),
                 ("graph_launches", ctypes.c_uint64), ("bytes_held", ctypes.c_uint64),
-                ("pending_readbacks", ctypes.c_int)]
+                ("pending_readbacks", ctypes.c_int), ("gpu_ms", ctypes.c_double)]
 
 
 # Exported symbols and their ctypes signatures (mirrors include/alto.h).

@@ -18,6 +18,7 @@ constexpr uint32_t kEmptyRow = 0xFFFFFFFFu;
 constexpr uint32_t kStatusCoordRange = 1u;
 constexpr uint32_t kStatusNotSpd = 2u;
 constexpr uint32_t kStatusTimeout = 4u;
+constexpr uint32_t kStatusPinv = 8u;  // a CP-ALS solve used the pseudo-inverse
 
 // One strided run of a mode's bits inside the linear index (Section III-A):
 // bits g0 .. g0+count-1 of the coordinate sit at key positions

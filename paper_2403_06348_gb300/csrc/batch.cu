@@ -242,6 +242,10 @@ struct alto_batch {
   std::vector<int> done_queue;
   uint64_t steps = 0, graph_launches = 0;
   size_t bytes_held = 0;
+  // device time of the enqueued steps: event pairs around each alto_batch_step
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timing;
+  std::vector<cudaEvent_t> event_pool;
+  double gpu_ms = 0.0;
 };
 
 namespace {
@@ -382,6 +386,39 @@ alto_status capture_graph(alto_batch *b) {
   return ALTO_OK;
 }
 
+cudaEvent_t timing_event(alto_batch *b) {
+  if (!b->event_pool.empty()) {
+    cudaEvent_t e = b->event_pool.back();
+    b->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Adds the device time of every finished step bracket to gpu_ms.
+void collect_timing(alto_batch *b) {
+  size_t keep = 0;
+  for (size_t i = 0; i < b->timing.size(); ++i) {
+    auto &pr = b->timing[i];
+    if (cudaEventQuery(pr.second) == cudaSuccess) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) b->gpu_ms += ms;
+      cudaGetLastError();
+      b->event_pool.push_back(pr.first);
+      b->event_pool.push_back(pr.second);
+    } else {
+      cudaGetLastError();
+      b->timing[keep++] = pr;
+    }
+  }
+  b->timing.resize(keep);
+}
+
 void process_readback(alto_batch *b, const Readback &r) {
   for (int i = 0; i < r.P && i < b->max_slots; ++i) {
     BatchSlot &sl = b->slots[i];
@@ -504,6 +541,11 @@ void alto_batch_free(alto_batch_t b) {
   bfree(b, b->unit_prob_dev, b->unit_cap * sizeof(uint32_t));
   bfree(b, b->tab, b->tab_bytes);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto &pr : b->timing) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (cudaEvent_t e : b->event_pool) cudaEventDestroy(e);
   for (int i = 0; i < kReadbackRing; ++i) {
     if (b->rb[i].ev) cudaEventDestroy(b->rb[i].ev);
     if (b->rb[i].host) cudaFreeHost(b->rb[i].host);
@@ -652,10 +694,17 @@ alto_status alto_batch_step(alto_batch_t b, int nsteps) {
     alto_status st = capture_graph(b);
     if (st != ALTO_OK) return st;
   }
+  cudaEvent_t t0 = timing_event(b), t1 = timing_event(b);
+  if (t0 && t1) CUDA_TRY(cudaEventRecord(t0, b->s));
   for (int i = 0; i < nsteps; ++i) {
     CUDA_TRY(cudaGraphLaunch(b->exec, b->s));
     note_launches(4);
   }
+  if (t0 && t1) {
+    CUDA_TRY(cudaEventRecord(t1, b->s));
+    b->timing.emplace_back(t0, t1);
+  }
+  collect_timing(b);
   b->steps += nsteps;
   b->graph_launches += nsteps;
   if (b->rb_count == kReadbackRing) {
@@ -739,6 +788,8 @@ alto_status alto_batch_query(alto_batch_t b, alto_batch_info *info) {
   info->graph_launches = b->graph_launches;
   info->bytes_held = b->bytes_held;
   info->pending_readbacks = b->rb_count;
+  collect_timing(b);
+  info->gpu_ms = b->gpu_ms;
   return ALTO_OK;
 }
 

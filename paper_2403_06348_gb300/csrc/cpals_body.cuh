@@ -16,6 +16,111 @@ inline size_t update_smem(int R) {
          (size_t)(R * R + R * (TR + 4) + TR * (R + 4)) * sizeof(float);
 }
 
+// Pseudo-inverse of the symmetric R x R matrix A (destroyed) into Y, with Q
+// as work space: cyclic Jacobi rotations in the round-robin order (R/2
+// disjoint pairs per step, R - 1 steps per sweep; Golub and Van Loan,
+// "parallel Jacobi") until the off-diagonal mass is below 1e-15 of the
+// total, then Y = Q diag(1/lambda) Q^T over the eigenvalues with |lambda| >
+// 1e-15 max |lambda| (the cut numpy's pinv makes). Returns false if A has a
+// non-finite entry. Called by all threads of the CTA.
+__device__ __forceinline__ bool pinv_body(double *A, double *Q, double *Y, int R, int lgR) {
+  const int tid = threadIdx.x, nt = blockDim.x, RR = R * R, half = R / 2;
+  __shared__ double c_s[ALTO_MAX_RANK / 2], s_s[ALTO_MAX_RANK / 2], red[2][32];
+  __shared__ int p_s[ALTO_MAX_RANK / 2], q_s[ALTO_MAX_RANK / 2];
+  const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+  bool finite = true;
+  for (int e = tid; e < RR; e += nt) {
+    Q[e] = ((e >> lgR) == (e & (R - 1))) ? 1.0 : 0.0;
+    finite = finite && isfinite(A[e]);
+  }
+  if (!__syncthreads_and(finite)) return false;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < RR; e += nt) {
+      const double v = A[e] * A[e];
+      tot += v;
+      if ((e >> lgR) != (e & (R - 1))) off += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = off;
+      red[1][warp] = tot;
+    }
+    __syncthreads();
+    off = tot = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      off += red[0][w];
+      tot += red[1][w];
+    }
+    __syncthreads();
+    if (!(off > 1e-30 * tot)) break;  // the same sums in every thread
+    for (int step = 0; step < R - 1; ++step) {
+      if (tid < half) {
+        int p, q;
+        if (tid == 0) {
+          p = step;
+          q = R - 1;
+        } else {
+          p = (step + tid) % (R - 1);
+          q = (step - tid + R - 1) % (R - 1);
+        }
+        const double apq = A[p * R + q];
+        double c = 1.0, sn = 0.0;
+        if (apq != 0.0) {
+          const double tau = (A[q * R + q] - A[p * R + p]) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          sn = t * c;
+        }
+        p_s[tid] = p;
+        q_s[tid] = q;
+        c_s[tid] = c;
+        s_s[tid] = sn;
+      }
+      __syncthreads();
+      for (int w = tid; w < half * R; w += nt) {  // rows p, q of every pair
+        const int k = w >> lgR, j = w & (R - 1);
+        const int p = p_s[k], q = q_s[k];
+        const double c = c_s[k], sn = s_s[k];
+        const double ap = A[p * R + j], aq = A[q * R + j];
+        A[p * R + j] = c * ap - sn * aq;
+        A[q * R + j] = sn * ap + c * aq;
+      }
+      __syncthreads();
+      for (int w = tid; w < half * R; w += nt) {  // columns p, q; Q accumulates J
+        const int k = w >> lgR, i = w & (R - 1);
+        const int p = p_s[k], q = q_s[k];
+        const double c = c_s[k], sn = s_s[k];
+        const double ap = A[i * R + p], aq = A[i * R + q];
+        A[i * R + p] = c * ap - sn * aq;
+        A[i * R + q] = sn * ap + c * aq;
+        const double qp = Q[i * R + p], qq = Q[i * R + q];
+        Q[i * R + p] = c * qp - sn * qq;
+        Q[i * R + q] = sn * qp + c * qq;
+      }
+      __syncthreads();
+    }
+  }
+  // eigenvalues on the diagonal; the cut relative to the largest
+  double mx = 0.0;
+  for (int k = 0; k < R; ++k) mx = fmax(mx, fabs(A[k * R + k]));
+  const double cut = 1e-15 * mx;
+  for (int e = tid; e < RR; e += nt) {
+    const int i = e >> lgR, j = e & (R - 1);
+    double acc = 0.0;
+    for (int k = 0; k < R; ++k) {
+      const double lk = A[k * R + k];
+      if (fabs(lk) > cut) acc += Q[i * R + k] * Q[j * R + k] / lk;
+    }
+    Y[e] = acc;
+  }
+  __syncthreads();
+  return true;
+}
+
 // V = Hadamard product of the other modes' Grams, its Cholesky factor L
 // (V = L L^T), X = L^-1, V^-1 = X^T X and W = diag(Sn) V^-1, all in fp64
 // inside one CTA. Every elimination step is one pass over the R x R square
@@ -47,14 +152,12 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
   __syncthreads();
   // Cholesky, right-looking: step k writes column k of L and updates the
   // trailing lower triangle (i >= j > k) of V from column k of V.
+  bool spd = true;
   for (int k = 0; k < R; ++k) {
     const double d = V[k * R + k];
     if (!(d > 0.0) || !isfinite(d)) {  // the same d in every thread
-      if (tid == 0) {
-        atomicOr(a.status, kStatusNotSpd);
-        *a.done_at = a.it;
-      }
-      return;
+      spd = false;
+      break;
     }
     const double inv_d = s_inv[k], rs = s_rs[k];
     for (int e = tid; e < RR; e += nt) {
@@ -72,6 +175,26 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     }
     __syncthreads();
   }
+  if (!spd) {
+    // V is not positive definite: the pseudo-inverse, as Alg. 1 states it,
+    // from the eigendecomposition of V (fp64 Jacobi). Only a V with a
+    // non-finite entry ends the run.
+    for (int e = tid; e < RR; e += nt) {
+      double v = 1.0;
+      for (int m = 0; m < a.N; ++m)
+        if (m != a.n) v *= a.G[(size_t)m * RR + e];
+      V[e] = v;
+    }
+    __syncthreads();
+    if (!pinv_body(V, L, Y, R, lgR)) {
+      if (tid == 0) {
+        atomicOr(a.status, kStatusNotSpd);
+        *a.done_at = a.it;
+      }
+      return;
+    }
+    if (tid == 0) atomicOr(a.status, kStatusPinv);
+  } else {
   // X = L^-1 by forward substitution on Y = I: step k finalises row k of X
   // (into V) and removes column k of L from the rows below.
   for (int k = 0; k < R; ++k) {
@@ -93,6 +216,7 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     for (int k = p; k < R; ++k) acc += V[k * R + p] * V[k * R + q];
     Y[p * R + q] = acc;
     Y[q * R + p] = acc;
+  }
   }
   for (int r = tid; r < R; r += nt) {
     double p = 1.0;
@@ -266,9 +390,19 @@ __device__ __forceinline__ void finish_body(const CpArgs &a) {
   double *Gn = a.G + (size_t)a.n * RR;
   for (int r = tid; r < R; r += blockDim.x) {
     const double g = a.BtB[r * R + r];
-    const double l = g > 0.0 ? sqrt(g) : 0.0;
+    lam[r] = g > 0.0 ? sqrt(g) : 0.0;
+  }
+  __syncthreads();
+  // a column of rounding noise (norm at most 1e-12 of the largest, left by a
+  // pseudo-inverse solve) is a zero column: lambda_r = 0 and s_r = 0
+  double lmax = 0.0;
+  for (int r = 0; r < R; ++r) lmax = fmax(lmax, lam[r]);
+  __syncthreads();
+  for (int r = tid; r < R; r += blockDim.x) {
+    double l = lam[r];
+    if (!(l > 1e-12 * lmax)) l = 0.0;
     lam[r] = l;
-    sn[r] = l > 0.0 ? 1.0 / l : 1.0;
+    sn[r] = l > 0.0 ? 1.0 / l : 0.0;
     a.lambda[r] = l;
     sv[r] = sn[r];
   }

@@ -101,6 +101,9 @@ class Server:
         self.work_nnz_r_iters = 0.0
         self.t_first: Optional[float] = None
         self.t_last: Optional[float] = None
+        # host seconds the loop thread spends per phase, and device time of the steps
+        self.loop_s = {"add": 0.0, "step_poll": 0.0, "retire_enqueue": 0.0, "retire_finish": 0.0}
+        self.batch_gpu_ms = 0.0
         self._admit_thread = threading.Thread(target=self._admit_loop, daemon=True)
         self._loop_thread = threading.Thread(target=self._loop, daemon=True)
         self._admit_thread.start()
@@ -132,11 +135,16 @@ class Server:
             self._lock.notify_all()
         self._admit_thread.join(timeout)
         self._loop_thread.join(timeout)
+        self.batch.sync()
+        self.batch_gpu_ms = self.batch.info().gpu_ms
         self.batch.free()
 
     def stats(self) -> dict:
         span = (self.t_last - self.t_first) if (self.t_first is not None and self.t_last) else float("nan")
         return {"completed": self.completed, "errors": self.errors,
+                "batch_gpu_s": self.batch_gpu_ms / 1000.0,
+                "gpu_busy_fraction": (self.batch_gpu_ms / 1000.0 / span) if span and span > 0 else float("nan"),
+                "loop_host_s": dict(self.loop_s),
                 "p50_s": percentile(self.latencies, 50), "p99_s": percentile(self.latencies, 99),
                 "mean_s": float(np.mean(self.latencies)) if self.latencies else float("nan"),
                 "requests_per_s": self.completed / span if span and span > 0 else float("nan"),
@@ -199,17 +207,24 @@ class Server:
                         return
                     self._lock.wait(0.002)
                     continue
+            t_a = time.perf_counter()
             for req in ready:
                 try:
                     slot = self.batch.add(req.tensor, req.R, req.iters, req.init, tol=req.tol)
                     self._live[slot] = req
                 except AltoError as e:
                     self._finish_error(req, e)
+            t_b = time.perf_counter()
+            self.loop_s["add"] += t_b - t_a
             if self._live:
                 self.batch.step(self.steps_per_round)
                 done = self.batch.poll(wait=False)
-                if not done and self.batch.info().pending_readbacks >= 2:
+                info = self.batch.info()
+                self.batch_gpu_ms = info.gpu_ms
+                if not done and info.pending_readbacks >= 2:
                     done = self.batch.poll(wait=True)
+                t_c = time.perf_counter()
+                self.loop_s["step_poll"] += t_c - t_b
                 for slot in done:
                     req = self._live.pop(slot)
                     outs = [torch.empty((d, req.R), dtype=torch.float32, pin_memory=True) for d in req.dims]
@@ -220,6 +235,8 @@ class Server:
                     ev.record(self.batch.stream)
                     self.batch.remove(slot)
                     self._retiring.append((ev, req, outs, lam, fits, iters_done, status))
+                self.loop_s["retire_enqueue"] += time.perf_counter() - t_c
+            t_d = time.perf_counter()
             still = []
             for item in self._retiring:
                 ev, req, outs, lam, fits, iters_done, status = item
@@ -241,6 +258,7 @@ class Server:
                     self._lock.notify_all()
                 req.future.set_result(res)
             self._retiring = still
+            self.loop_s["retire_finish"] += time.perf_counter() - t_d
             if not self._live and self._retiring:
                 time.sleep(0.0002)
 

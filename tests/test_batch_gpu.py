@@ -3,8 +3,9 @@
 Each run's fit trajectory must follow the fp64 oracle's (|dfit| <= 1e-4 per
 iteration, the cpals_run bar) and match the same run done alone with
 cpals_run, whether it ran alone in the batch or in a mix whose members join
-and leave at different steps. A run that fails (V not positive definite)
-reports NOT_SPD without disturbing the others.
+and leave at different steps. A run with a singular V goes on through the
+pseudo-inverse; a run with a non-finite V reports NOT_SPD; neither disturbs
+the others.
 """
 import numpy as np
 import pytest
@@ -126,22 +127,28 @@ def test_runs_join_and_leave_between_steps():
     batch.free()
 
 
-def test_tol_stop_and_not_spd_in_the_mix():
+def test_tol_stop_pinv_and_not_spd_in_the_mix():
     import paper_2403_06348_gb300 as alto
     good = Run(20, (300, 200, 100), 20_000, 8, 40, tol=1e-3)
-    bad = Run(21, (60, 50, 40), 3_000, 4, 5)
-    for a in bad.init:
-        a[:, 1] = 0.0  # a zero column in every factor: V has a zero pivot
+    sing = Run(21, (60, 50, 40), 3_000, 4, 5)
+    for a in sing.init:
+        a[:, 1] = 0.0  # a zero column in every factor: V is singular (pseudo-inverse)
+    bad = Run(23, (60, 50, 40), 3_000, 4, 5)
+    bad.init[1][7, 2] = np.inf  # a non-finite V: the run ends with NOT_SPD
     plain = Run(22, (500, 400, 30), 15_000, 16, 4)
     batch = alto.Batch(max_slots=8)
     sg = batch.add(good.t, good.R, good.iters, gu.gpu_factors(good.init), tol=good.tol)
+    ss = batch.add(sing.t, sing.R, sing.iters, gu.gpu_factors(sing.init))
     sb = batch.add(bad.t, bad.R, bad.iters, gu.gpu_factors(bad.init))
     sp = batch.add(plain.t, plain.R, plain.iters, gu.gpu_factors(plain.init))
-    _run_to_end(batch, [sg, sb, sp])
+    _run_to_end(batch, [sg, ss, sb, sp])
     _, _, fits_g, st_g = good.fetch(batch, sg)
+    _, _, fits_s, st_s = sing.fetch(batch, ss)
     _, _, _, st_b = bad.fetch(batch, sb)
     _, _, fits_p, st_p = plain.fetch(batch, sp)
-    assert st_b == -6 and st_g == 0 and st_p == 0
+    assert st_b == -6 and st_g == 0 and st_p == 0 and st_s == 0
+    ref_s = _oracle_fits(sing.coords, sing.vals, sing.dims, sing.init, sing.iters)
+    np.testing.assert_allclose(fits_s, ref_s.fits, atol=FIT_TOL)
     _, _, alone_g = good.alone()
     assert 1 < len(fits_g) < good.iters and len(fits_g) == len(alone_g)
     np.testing.assert_allclose(fits_g, alone_g, atol=FIT_TOL)

@@ -91,14 +91,31 @@ def test_tol_stops_early_and_host_factors_match_device():
         np.testing.assert_allclose(a, b.cpu().numpy(), atol=1e-4)
 
 
-def test_singular_gram_reports_not_spd():
-    import paper_2403_06348_gb300 as alto
+def test_singular_gram_falls_back_to_pinv():
+    """A zero column in every factor makes V singular: the solve uses the
+    pseudo-inverse (fp64 Jacobi on the GPU, numpy's pinv in the oracle) and the
+    trajectory still follows the oracle; the zero column stays zero."""
     dims = (30, 20, 10)
     coords, vals = gu.rand_tensor(dims, 2000, 4)
     t = gu.encode(coords, vals, dims)
     init = gu.rand_factors(dims, 4, 6)
     for a in init:
         a[:, 1] = 0.0          # a zero column in every factor: V has a zero pivot
+    ref = _oracle_cpals(coords, vals, dims, init, iters=3)
+    A = gu.gpu_factors(init)
+    lam, fits = t.cpals(4, 3, A)
+    np.testing.assert_allclose(fits, ref.fits, atol=1e-4)
+    for a in A:
+        assert float(a[:, 1].abs().max()) == 0.0
+
+
+def test_non_finite_factors_report_not_spd():
+    import paper_2403_06348_gb300 as alto
+    dims = (30, 20, 10)
+    coords, vals = gu.rand_tensor(dims, 2000, 4)
+    t = gu.encode(coords, vals, dims)
+    init = gu.rand_factors(dims, 4, 6)
+    init[2][3, 1] = np.nan
     A = gu.gpu_factors(init)
     with pytest.raises(alto.AltoError) as e:
         t.cpals(4, 3, A)

@@ -121,3 +121,23 @@ def test_singular_gram_uses_pinv():
     An = ar._solve_spd_or_pinv(V, M0)
     assert np.all(np.isfinite(An))
     np.testing.assert_allclose(An[:, 0], An[:, 1], rtol=1e-9)
+
+
+def test_zero_column_stays_exactly_zero_through_pinv():
+    """A zero column in every initial factor makes every V singular; the pinv
+    solution leaves that column at rounding level, which the normalisation
+    reads as zero: the column stays exactly 0 with lambda 0, and the other
+    columns match a rank-(R-1) run without it."""
+    rng = np.random.default_rng(21)
+    dims = (12, 9, 7)
+    coords = np.stack([rng.integers(0, d, 300) for d in dims]).astype(np.uint32)
+    vals = rng.random(300)
+    init = [rng.random((d, 3)) for d in dims]
+    padded = [np.insert(a, 1, 0.0, axis=1) for a in init]
+    full = ar.cp_als(coords, vals, dims, padded, 4)
+    small = ar.cp_als(coords, vals, dims, init, 4)
+    np.testing.assert_allclose(full.fits, small.fits, rtol=1e-9)
+    assert full.lam[1] == 0.0
+    for a, b in zip(full.factors, small.factors):
+        assert np.all(a[:, 1] == 0.0)
+        np.testing.assert_allclose(np.delete(a, 1, axis=1), b, rtol=1e-7, atol=1e-10)
