@@ -402,6 +402,11 @@ alto_status cpapr_run(alto_handle_t h, int R, const alto_apr_params *params, flo
  *                    nonzeros, and reads h until alto_batch_remove. *slot
  *                    receives the run's slot. Errors: INVALID_ARG,
  *                    UNSUPPORTED (rank, no free slot), OOM, CUDA.
+ * alto_batch_prepare  the per-handle set-up alto_batch_add needs (segments of
+ *                    about 4096 nonzeros, rank-ordered decode runs, hot-row
+ *                    tables for rank R), done on the handle's stream and
+ *                    waited for; call it where waiting is cheap (e.g. right
+ *                    after alto_encode) and alto_batch_add then finds it done.
  * alto_batch_step    enqueues nsteps steps and one asynchronous read-back of
  *                    the runs' states; returns without waiting (it waits only
  *                    when four read-backs are still outstanding).
@@ -440,6 +445,7 @@ alto_status alto_batch_create(int max_slots, const alto_allocator *alloc, void *
 void alto_batch_free(alto_batch_t b);
 alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, double tol,
                            const float *const *factors, int *slot);
+alto_status alto_batch_prepare(alto_handle_t h, int R);
 alto_status alto_batch_step(alto_batch_t b, int nsteps);
 alto_status alto_batch_poll(alto_batch_t b, int wait, int *slots, int cap, int *ndone);
 alto_status alto_batch_result(alto_batch_t b, int slot, float *const *factors, double *lambda,

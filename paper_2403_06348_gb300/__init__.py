@@ -119,6 +119,7 @@ SIGNATURES = {
     "alto_batch_create": ([_i32, _vp, _vp, ctypes.POINTER(_vp)], _i32),
     "alto_batch_free": ([_vp], None),
     "alto_batch_add": ([_vp, _vp, _i32, _i32, ctypes.c_double, _vp, ctypes.POINTER(_i32)], _i32),
+    "alto_batch_prepare": ([_vp, _i32], _i32),
     "alto_batch_step": ([_vp, _i32], _i32),
     "alto_batch_poll": ([_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)], _i32),
     "alto_batch_result": ([_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
@@ -312,6 +313,11 @@ class Batch:
                                     ctypes.byref(slot)))
         self._tensors[slot.value] = t
         return int(slot.value)
+
+    @staticmethod
+    def prepare(t: "AltoTensor", R: int) -> None:
+        """alto_batch_prepare: the handle's batch set-up, on its own stream."""
+        _check(lib().alto_batch_prepare(t.handle, int(R)))
 
     def step(self, nsteps: int = 1) -> None:
         _check(lib().alto_batch_step(self._b, int(nsteps)))

@@ -556,6 +556,22 @@ void alto_batch_free(alto_batch_t b) {
   delete b;
 }
 
+alto_status alto_batch_prepare(alto_handle_t h, int R) {
+  if (!h) return fail(ALTO_ERR_INVALID_ARG, "null handle");
+  if (!(R == 4 || R == 8 || R == 16 || R == 32 || R == 64))
+    return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
+  cudaStream_t hs = h->stream;
+  const uint64_t want_L = std::max<uint64_t>(1, (h->M + kBatchSegNnz - 1) / kBatchSegNnz);
+  if (h->M > 0 && h->L > 2 * want_L) {
+    alto_status st = repartition(h, want_L, hs);
+    if (st != ALTO_OK) return st;
+  }
+  alto_status st = ensure_rank_runs(h, hs);
+  if (st != ALTO_OK) return st;
+  GroupProb gp{};
+  return fill_group_prob(h, R, &gp, hs);
+}
+
 alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, double tol,
                            const float *const *factors, int *slot_out) {
   if (!b || !h) return fail(ALTO_ERR_INVALID_ARG, "null batch or handle");
@@ -578,17 +594,13 @@ alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, do
       break;
     }
   if (slot < 0) return fail(ALTO_ERR_UNSUPPORTED, "all %d batch slots are in use", b->max_slots);
-  // on the handle's stream: segments of about kBatchSegNnz nonzeros, rank runs
+  // on the handle's stream (free after alto_batch_prepare): segments of
+  // about kBatchSegNnz nonzeros, rank runs, grouped hot-row tables
   cudaStream_t hs = h->stream;
-  const uint64_t want_L = std::max<uint64_t>(1, (h->M + kBatchSegNnz - 1) / kBatchSegNnz);
-  if (h->L > 2 * want_L) {
-    alto_status st = repartition(h, want_L, hs);
-    if (st != ALTO_OK) return st;
-  }
-  alto_status st = ensure_rank_runs(h, hs);
+  alto_status st = alto_batch_prepare(h, R);
   if (st != ALTO_OK) return st;
   GroupProb gp{};
-  st = fill_group_prob(h, R, &gp, hs);  // hot-row tables on the handle's stream
+  st = fill_group_prob(h, R, &gp, hs);
   if (st != ALTO_OK) return st;
   CUDA_TRY(cudaEventRecord(b->order_ev, hs));
   CUDA_TRY(cudaStreamWaitEvent(b->s, b->order_ev, 0));

@@ -6,9 +6,11 @@ returns a Future. An admission thread encodes requests on its own stream
 resident bytes of the runs in flight plus its own peak bytes
 (alto_cpals_footprint) stay within the budget and a batch slot is free. The
 loop thread adds encoded requests to the batch, advances every active run by
-one mode update per step (alto_batch_step, a replayed CUDA graph), polls the
-asynchronous state read-backs, and retires finished runs (normalised factors,
-lambda and fits copied into pinned host memory). Requests that arrive while
+one mode update per step (alto_batch_step, a replayed CUDA graph; two steps
+per round, up to three rounds queued ahead of the host), polls the
+asynchronous state read-backs, and moves finished runs' results (normalised
+factors, lambda, fits) into device buffers; a retire thread copies them to
+the host and completes the futures. Requests that arrive while
 others are on the GPU join at the next step, so their work overlaps.
 
 ``run_fcfs`` is the one-at-a-time reference: the same library, one request
@@ -80,7 +82,7 @@ def percentile(xs: Sequence[float], q: float) -> float:
 class Server:
     """Continuous-batching CP-ALS server (see module docstring)."""
 
-    def __init__(self, budget_bytes: float = 100e9, max_slots: int = 1024, steps_per_round: int = 4):
+    def __init__(self, budget_bytes: float = 100e9, max_slots: int = 1024, steps_per_round: int = 2):
         import torch
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
@@ -104,10 +106,13 @@ class Server:
         # host seconds the loop thread spends per phase, and device time of the steps
         self.loop_s = {"add": 0.0, "step_poll": 0.0, "retire_enqueue": 0.0, "retire_finish": 0.0}
         self.batch_gpu_ms = 0.0
+        self._loop_done = False
         self._admit_thread = threading.Thread(target=self._admit_loop, daemon=True)
         self._loop_thread = threading.Thread(target=self._loop, daemon=True)
+        self._retire_thread = threading.Thread(target=self._retire_loop, daemon=True)
         self._admit_thread.start()
         self._loop_thread.start()
+        self._retire_thread.start()
 
     # -- public --------------------------------------------------------------
     def submit(self, coords: np.ndarray, vals: np.ndarray, dims: Sequence[int], R: int, iters: int,
@@ -135,6 +140,7 @@ class Server:
             self._lock.notify_all()
         self._admit_thread.join(timeout)
         self._loop_thread.join(timeout)
+        self._retire_thread.join(timeout)
         self.batch.sync()
         self.batch_gpu_ms = self.batch.info().gpu_ms
         self.batch.free()
@@ -168,6 +174,7 @@ class Server:
             try:
                 with torch.cuda.stream(self.encode_stream):
                     req.tensor = alto_encode(req.coords, req.vals, req.dims, stream=self.encode_stream)
+                    Batch.prepare(req.tensor, req.R)  # its waits stay off the loop thread
                     # initial factors on the encode stream (the batch orders
                     # itself after the handle's stream)
                     if req.init is None:
@@ -201,9 +208,11 @@ class Server:
             with self._lock:
                 ready = list(self._ready)
                 self._ready.clear()
-                idle = not ready and not self._live and not self._retiring
+                idle = not ready and not self._live
                 if idle:
                     if self._stop and not self._waiting and self._admitted == 0:
+                        self._loop_done = True
+                        self._lock.notify_all()
                         return
                     self._lock.wait(0.002)
                     continue
@@ -221,46 +230,59 @@ class Server:
                 done = self.batch.poll(wait=False)
                 info = self.batch.info()
                 self.batch_gpu_ms = info.gpu_ms
-                if not done and info.pending_readbacks >= 2:
+                if not done and info.pending_readbacks >= 3:  # keep ~3 rounds queued on the GPU
                     done = self.batch.poll(wait=True)
                 t_c = time.perf_counter()
                 self.loop_s["step_poll"] += t_c - t_b
                 for slot in done:
                     req = self._live.pop(slot)
-                    outs = [torch.empty((d, req.R), dtype=torch.float32, pin_memory=True) for d in req.dims]
-                    lam = torch.empty(req.R, dtype=torch.float64, pin_memory=True)
-                    fits = torch.zeros(req.iters, dtype=torch.float64, pin_memory=True)
+                    # results land in device buffers (stream-ordered, no host
+                    # allocation here); the retire thread copies them out
+                    outs = [torch.empty((d, req.R), dtype=torch.float32, device="cuda") for d in req.dims]
+                    lam = torch.empty(req.R, dtype=torch.float64, device="cuda")
+                    fits = torch.zeros(req.iters, dtype=torch.float64, device="cuda")
                     iters_done, status = self.batch.result(slot, outs, lam, fits)
                     ev = torch.cuda.Event()
                     ev.record(self.batch.stream)
                     self.batch.remove(slot)
-                    self._retiring.append((ev, req, outs, lam, fits, iters_done, status))
+                    with self._lock:
+                        self._retiring.append((ev, req, outs, lam, fits, iters_done, status))
+                        self._lock.notify_all()
                 self.loop_s["retire_enqueue"] += time.perf_counter() - t_c
-            t_d = time.perf_counter()
-            still = []
-            for item in self._retiring:
-                ev, req, outs, lam, fits, iters_done, status = item
-                if not ev.query():
-                    still.append(item)
-                    continue
-                now = time.perf_counter()
-                res = CPResult([o.numpy() for o in outs], lam.numpy(), fits.numpy()[:iters_done].tolist(),
-                               iters_done, status, req.arrival, req.admitted, now)
-                req.tensor.free()
-                req.tensor = None
+            elif not ready:
                 with self._lock:
-                    self._resident -= req.resident
-                    self._admitted -= 1
-                    self.completed += 1
-                    self.latencies.append(res.latency)
-                    self.work_nnz_r_iters += float(req.vals.shape[0]) * req.R * iters_done
-                    self.t_last = now
-                    self._lock.notify_all()
-                req.future.set_result(res)
-            self._retiring = still
-            self.loop_s["retire_finish"] += time.perf_counter() - t_d
-            if not self._live and self._retiring:
-                time.sleep(0.0002)
+                    self._lock.wait(0.001)
+
+    # -- retire thread: copy results out, finish the futures -----------------
+    def _retire_loop(self) -> None:
+        import torch
+        while True:
+            with self._lock:
+                while not self._retiring and not (self._stop and self._loop_done):
+                    self._lock.wait(0.002)
+                if not self._retiring:
+                    return
+                item = self._retiring.pop(0)
+            t0 = time.perf_counter()
+            ev, req, outs, lam, fits, iters_done, status = item
+            ev.synchronize()
+            res_f = [o.cpu().numpy() for o in outs]
+            lam_h = lam.cpu().numpy()
+            fits_h = fits.cpu().numpy()[:iters_done].tolist()
+            now = time.perf_counter()
+            res = CPResult(res_f, lam_h, fits_h, iters_done, status, req.arrival, req.admitted, now)
+            req.tensor.free()
+            req.tensor = None
+            with self._lock:
+                self._resident -= req.resident
+                self._admitted -= 1
+                self.completed += 1
+                self.latencies.append(res.latency)
+                self.work_nnz_r_iters += float(req.vals.shape[0]) * req.R * iters_done
+                self.t_last = now
+                self.loop_s["retire_finish"] += now - t0
+                self._lock.notify_all()
+            req.future.set_result(res)
 
     def _finish_error(self, req: _Request, e: Exception) -> None:
         if req.tensor is not None:
@@ -303,9 +325,7 @@ def run_fcfs(requests, schedule_start: float) -> dict:
                 raise
             not_spd += 1
             fits = []
-        outs = [torch.empty(a.shape, dtype=torch.float32, pin_memory=True) for a in A]
-        for o, a in zip(outs, A):
-            o.copy_(a)
+        outs = [a.cpu().numpy() for a in A]  # results on the host, as the Server delivers them
         t.free()
         t_last = time.perf_counter()
         lat.append(t_last - arrival)
