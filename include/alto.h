@@ -421,6 +421,12 @@ alto_status cpapr_run(alto_handle_t h, int R, const alto_apr_params *params, flo
  *                    alto_batch_sync (pin them for asynchronous copies).
  *                    *iters_done and *run_status (ALTO_OK or
  *                    ALTO_ERR_NOT_SPD) come from the read-back.
+ * alto_batch_copy_out  after alto_batch_result (which may pass NULL
+ *                    destinations and then only normalises in place): copies
+ *                    the slot's factors, lambda and fits into host or device
+ *                    buffers on `stream` and waits for them. It reads only
+ *                    that slot, so another host thread may call it while the
+ *                    batch goes on, until the slot is removed.
  * alto_batch_remove  frees the slot (stream-ordered) and orders the handle's
  *                    stream after the batch, so the handle may then be freed.
  * alto_batch_sync    waits for everything enqueued on the batch stream.
@@ -450,6 +456,8 @@ alto_status alto_batch_step(alto_batch_t b, int nsteps);
 alto_status alto_batch_poll(alto_batch_t b, int wait, int *slots, int cap, int *ndone);
 alto_status alto_batch_result(alto_batch_t b, int slot, float *const *factors, double *lambda,
                               double *fits, int *iters_done, int *run_status);
+alto_status alto_batch_copy_out(alto_batch_t b, int slot, float *const *factors, double *lambda,
+                                double *fits, void *stream);
 alto_status alto_batch_remove(alto_batch_t b, int slot);
 alto_status alto_batch_query(alto_batch_t b, alto_batch_info *info);
 alto_status alto_batch_sync(alto_batch_t b);

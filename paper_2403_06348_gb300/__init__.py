@@ -124,6 +124,7 @@ SIGNATURES = {
     "alto_batch_poll": ([_vp, _i32, _vp, _i32, ctypes.POINTER(_i32)], _i32),
     "alto_batch_result": ([_vp, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
                           _i32),
+    "alto_batch_copy_out": ([_vp, _i32, _vp, _vp, _vp, _vp], _i32),
     "alto_batch_remove": ([_vp, _i32], _i32),
     "alto_batch_query": ([_vp, ctypes.POINTER(alto_batch_info)], _i32),
     "alto_batch_sync": ([_vp], _i32),
@@ -339,6 +340,15 @@ class Batch:
                                        ctypes.byref(st)))
         _torch().cuda.current_stream().wait_stream(self.stream)
         return int(done.value), int(st.value)
+
+    def copy_out(self, slot: int, factors, lam=None, fits=None, stream=None) -> None:
+        """alto_batch_copy_out: the slot's results (after result()) into the
+        given buffers; may run on another thread until remove()."""
+        t = self._tensors[slot]
+        arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
+        _check(lib().alto_batch_copy_out(self._b, int(slot), arr, _ptr(lam) if lam is not None else None,
+                                         _ptr(fits) if fits is not None else None,
+                                         _stream_ptr(stream)))
 
     def remove(self, slot: int) -> None:
         _check(lib().alto_batch_remove(self._b, int(slot)))

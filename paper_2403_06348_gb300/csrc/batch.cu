@@ -202,6 +202,7 @@ struct BatchSlot {
   GroupProb gp{};
   CpState last{};
   bool reported = false;
+  cudaEvent_t result_ev = nullptr;  // recorded by alto_batch_result
 };
 
 struct Readback {
@@ -536,8 +537,10 @@ alto_status alto_batch_create(int max_slots, const alto_allocator *alloc, void *
 void alto_batch_free(alto_batch_t b) {
   if (!b) return;
   if (b->s) cudaStreamSynchronize(b->s);
-  for (int i = 0; i < b->max_slots; ++i)
+  for (int i = 0; i < b->max_slots; ++i) {
     if (b->slots[i].used) bfree(b, b->slots[i].ws, b->slots[i].ws_bytes);
+    if (b->slots[i].result_ev) cudaEventDestroy(b->slots[i].result_ev);
+  }
   bfree(b, b->unit_prob_dev, b->unit_cap * sizeof(uint32_t));
   bfree(b, b->tab, b->tab_bytes);
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -767,8 +770,28 @@ alto_status alto_batch_result(alto_batch_t b, int slot, float *const *factors, d
   }
   if (lambda) CUDA_TRY(cudaMemcpyAsync(lambda, cp.lambda, (size_t)R * 8, cudaMemcpyDefault, s));
   if (fits) CUDA_TRY(cudaMemcpyAsync(fits, cp.fits, (size_t)cp.iters * 8, cudaMemcpyDefault, s));
+  if (!sl.result_ev) CUDA_TRY(cudaEventCreateWithFlags(&sl.result_ev, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventRecord(sl.result_ev, s));
   if (iters_done) *iters_done = sl.last.iters_done;
   if (run_status) *run_status = (sl.last.status & kStatusNotSpd) ? ALTO_ERR_NOT_SPD : ALTO_OK;
+  return ALTO_OK;
+}
+
+alto_status alto_batch_copy_out(alto_batch_t b, int slot, float *const *factors, double *lambda,
+                                double *fits, void *stream) {
+  if (!b || slot < 0 || slot >= b->max_slots || !b->slots[slot].used)
+    return fail(ALTO_ERR_INVALID_ARG, "slot %d is not in use", slot);
+  const BatchSlot &sl = b->slots[slot];
+  if (!sl.result_ev) return fail(ALTO_ERR_INVALID_ARG, "slot %d: call alto_batch_result first", slot);
+  const CpProb &cp = sl.cp;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaStreamWaitEvent(s, sl.result_ev, 0));
+  for (int m = 0; m < cp.N; ++m)
+    if (factors && factors[m])
+      CUDA_TRY(cudaMemcpyAsync(factors[m], cp.B[m], cp.dims[m] * cp.R * 4, cudaMemcpyDefault, s));
+  if (lambda) CUDA_TRY(cudaMemcpyAsync(lambda, cp.lambda, (size_t)cp.R * 8, cudaMemcpyDefault, s));
+  if (fits) CUDA_TRY(cudaMemcpyAsync(fits, cp.fits, (size_t)cp.iters * 8, cudaMemcpyDefault, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   return ALTO_OK;
 }
 
@@ -777,6 +800,7 @@ alto_status alto_batch_remove(alto_batch_t b, int slot) {
     return fail(ALTO_ERR_INVALID_ARG, "slot %d is not in use", slot);
   BatchSlot &sl = b->slots[slot];
   bfree(b, sl.ws, sl.ws_bytes);
+  if (sl.result_ev) cudaEventDestroy(sl.result_ev);
   // the handle may be freed on its own stream once the batch is done with it
   CUDA_TRY(cudaEventRecord(b->order_ev, b->s));
   CUDA_TRY(cudaStreamWaitEvent(sl.h->stream, b->order_ev, 0));

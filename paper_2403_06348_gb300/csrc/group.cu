@@ -120,12 +120,14 @@ __device__ __noinline__ void group_segment(const GroupUnit &g, const DecodePlan3
     int slot = -1;
     if (valid) slot = staged ? (int)(row - Ts) : (hot ? hot_lookup(shtab, hbits, row) : -1);
     const uint64_t rem = s1 - base;
+    // many small tensors stage heavily shared rows: rotate the flush order per
+    // group so groups on the same row add to different columns
     if (rem >= 32)
-      group_rounds<NMAX, CPL, BF16, false>(fb, out, R, N, tpn, grp, sub, v, slot, row, in, 32, temp,
-                                           rowb);
+      group_rounds<NMAX, CPL, BF16, false, kAprOff, true>(fb, out, R, N, tpn, grp, sub, v, slot, row,
+                                                          in, 32, temp, rowb);
     else
-      group_rounds<NMAX, CPL, BF16, true>(fb, out, R, N, tpn, grp, sub, v, slot, row, in, (int)rem,
-                                          temp, rowb);
+      group_rounds<NMAX, CPL, BF16, true, kAprOff, true>(fb, out, R, N, tpn, grp, sub, v, slot, row,
+                                                         in, (int)rem, temp, rowb);
   }
 }
 

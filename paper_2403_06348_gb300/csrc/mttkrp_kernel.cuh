@@ -95,14 +95,14 @@ __device__ __forceinline__ uint32_t lane_byte_offset(int sub) {
 // Shared-memory flushes: at step k, the lanes of group g add element
 // (k + g) mod 4 of their 4-column vector, so groups flushing in the same
 // instruction use different banks (each group's lanes cover a whole row).
-template <int CPL>
+template <int CPL, bool ROT = (CPL >= 8)>
 __device__ __forceinline__ void flush_run(const float (&run)[CPL], uint32_t row, int slot,
                                           float *temp, float *out, int R, int sub, int tpn,
                                           int grp) {
   if (slot >= 0) {
     float *t = temp + (size_t)slot * R;
     const int sw = slot_swizzle(slot, R);
-    const int rot = (ALTO_HOT_ROTATE && CPL >= 8) ? (grp & 3) : 0;
+    const int rot = (ALTO_HOT_ROTATE && ROT) ? (grp & 3) : 0;
 #pragma unroll
     for (int v = 0; v < CPL / 4; ++v) {
       const int col = lane_col<CPL>(sub, v, tpn) ^ sw;
@@ -217,7 +217,7 @@ struct AprArgs {
   uint64_t pos0;       // ordered position of the batch's first nonzero
 };
 
-template <int NMAX, int CPL, bool BF16, bool TAIL, int APR = kAprOff>
+template <int NMAX, int CPL, bool BF16, bool TAIL, int APR = kAprOff, bool ROT = (CPL >= 8)>
 __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? NMAX - 1 : 1],
                                              float *out, int R, int N, int tpn, int grp, int sub,
                                              float v, int slot, uint32_t row,
@@ -326,14 +326,14 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] += p[c];
     } else {
-      if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn, grp);
+      if (run_row != kEmptyRow) flush_run<CPL, ROT>(run, run_row, run_slot, temp, out, R, sub, tpn, grp);
 #pragma unroll
       for (int c = 0; c < CPL; ++c) run[c] = p[c];
       run_row = rj;
       run_slot = sj;
     }
   }
-  if (run_row != kEmptyRow) flush_run<CPL>(run, run_row, run_slot, temp, out, R, sub, tpn, grp);
+  if (run_row != kEmptyRow) flush_run<CPL, ROT>(run, run_row, run_slot, temp, out, R, sub, tpn, grp);
 }
 
 // Wider lanes (8 or 16 columns) keep twice the values in registers: those

@@ -8,9 +8,10 @@ resident bytes of the runs in flight plus its own peak bytes
 loop thread adds encoded requests to the batch, advances every active run by
 one mode update per step (alto_batch_step, a replayed CUDA graph; two steps
 per round, up to three rounds queued ahead of the host), polls the
-asynchronous state read-backs, and moves finished runs' results (normalised
-factors, lambda, fits) into device buffers; a retire thread copies them to
-the host and completes the futures. Requests that arrive while
+asynchronous state read-backs, and normalises finished runs in place; a
+retire thread copies their results (factors, lambda, fits) to the host
+(alto_batch_copy_out) and completes the futures, and the loop thread then
+frees the slots. Requests that arrive while
 others are on the GPU join at the next step, so their work overlaps.
 
 ``run_fcfs`` is the one-at-a-time reference: the same library, one request
@@ -93,7 +94,7 @@ class Server:
         self._waiting: collections.deque = collections.deque()   # submitted, not encoded
         self._ready: collections.deque = collections.deque()     # encoded, not in the batch
         self._live = {}                                          # slot -> request
-        self._retiring: list = []                                # (event, request, buffers)
+        self._retiring: list = []                                # (slot, request, iters, status)
         self._resident = 0
         self._admitted = 0
         self._stop = False
@@ -107,6 +108,8 @@ class Server:
         self.loop_s = {"add": 0.0, "step_poll": 0.0, "retire_enqueue": 0.0, "retire_finish": 0.0}
         self.batch_gpu_ms = 0.0
         self._loop_done = False
+        self._to_remove: list = []
+        self.retire_stream = torch.cuda.Stream()
         self._admit_thread = threading.Thread(target=self._admit_loop, daemon=True)
         self._loop_thread = threading.Thread(target=self._loop, daemon=True)
         self._retire_thread = threading.Thread(target=self._retire_loop, daemon=True)
@@ -208,15 +211,22 @@ class Server:
             with self._lock:
                 ready = list(self._ready)
                 self._ready.clear()
-                idle = not ready and not self._live
+                idle = not ready and not self._live and not self._to_remove
                 if idle:
-                    if self._stop and not self._waiting and self._admitted == 0:
+                    if self._stop and not self._waiting and self._admitted == 0 and not self._retiring:
                         self._loop_done = True
                         self._lock.notify_all()
                         return
                     self._lock.wait(0.002)
                     continue
             t_a = time.perf_counter()
+            with self._lock:
+                gone = self._to_remove
+                self._to_remove = []
+            for slot, req in gone:
+                self.batch.remove(slot)
+                req.tensor.free()
+                req.tensor = None
             for req in ready:
                 try:
                     slot = self.batch.add(req.tensor, req.R, req.iters, req.init, tol=req.tol)
@@ -236,17 +246,11 @@ class Server:
                 self.loop_s["step_poll"] += t_c - t_b
                 for slot in done:
                     req = self._live.pop(slot)
-                    # results land in device buffers (stream-ordered, no host
-                    # allocation here); the retire thread copies them out
-                    outs = [torch.empty((d, req.R), dtype=torch.float32, device="cuda") for d in req.dims]
-                    lam = torch.empty(req.R, dtype=torch.float64, device="cuda")
-                    fits = torch.zeros(req.iters, dtype=torch.float64, device="cuda")
-                    iters_done, status = self.batch.result(slot, outs, lam, fits)
-                    ev = torch.cuda.Event()
-                    ev.record(self.batch.stream)
-                    self.batch.remove(slot)
+                    # normalise in place; the retire thread copies the slot
+                    # out (alto_batch_copy_out) and hands it back for removal
+                    iters_done, status = self.batch.result(slot, [None] * len(req.dims))
                     with self._lock:
-                        self._retiring.append((ev, req, outs, lam, fits, iters_done, status))
+                        self._retiring.append((slot, req, iters_done, status))
                         self._lock.notify_all()
                 self.loop_s["retire_enqueue"] += time.perf_counter() - t_c
             elif not ready:
@@ -264,16 +268,16 @@ class Server:
                     return
                 item = self._retiring.pop(0)
             t0 = time.perf_counter()
-            ev, req, outs, lam, fits, iters_done, status = item
-            ev.synchronize()
-            res_f = [o.cpu().numpy() for o in outs]
-            lam_h = lam.cpu().numpy()
-            fits_h = fits.cpu().numpy()[:iters_done].tolist()
+            slot, req, iters_done, status = item
+            res_f = [np.empty((d, req.R), dtype=np.float32) for d in req.dims]
+            lam_h = np.empty(req.R)
+            fits_h = np.zeros(req.iters)
+            self.batch.copy_out(slot, res_f, lam_h, fits_h, stream=self.retire_stream)
             now = time.perf_counter()
-            res = CPResult(res_f, lam_h, fits_h, iters_done, status, req.arrival, req.admitted, now)
-            req.tensor.free()
-            req.tensor = None
+            res = CPResult(res_f, lam_h, fits_h[:iters_done].tolist(), iters_done, status, req.arrival,
+                           req.admitted, now)
             with self._lock:
+                self._to_remove.append((slot, req))
                 self._resident -= req.resident
                 self._admitted -= 1
                 self.completed += 1
