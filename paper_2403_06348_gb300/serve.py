@@ -83,7 +83,8 @@ def percentile(xs: Sequence[float], q: float) -> float:
 class Server:
     """Continuous-batching CP-ALS server (see module docstring)."""
 
-    def __init__(self, budget_bytes: float = 100e9, max_slots: int = 1024, steps_per_round: int = 2):
+    def __init__(self, budget_bytes: float = 100e9, max_slots: int = 1024, steps_per_round: int = 2,
+                 staging_bytes: int = 256 << 20):
         import torch
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
@@ -105,11 +106,17 @@ class Server:
         self.t_first: Optional[float] = None
         self.t_last: Optional[float] = None
         # host seconds the loop thread spends per phase, and device time of the steps
-        self.loop_s = {"add": 0.0, "step_poll": 0.0, "retire_enqueue": 0.0, "retire_finish": 0.0}
+        self.loop_s = {"add": 0.0, "step_poll": 0.0, "retire_enqueue": 0.0, "retire_finish": 0.0,
+                       "remove": 0.0, "free": 0.0, "batch_add": 0.0}
         self.batch_gpu_ms = 0.0
         self._loop_done = False
         self._to_remove: list = []
         self.retire_stream = torch.cuda.Stream()
+        # Page-locked staging for uploads (admission thread) and downloads
+        # (retire thread): copies from pageable memory go through the driver's
+        # own staging and slow every other thread's CUDA calls meanwhile.
+        self._up = torch.empty(staging_bytes, dtype=torch.uint8, pin_memory=True).numpy()
+        self._down = torch.empty(staging_bytes, dtype=torch.uint8, pin_memory=True).numpy()
         self._admit_thread = threading.Thread(target=self._admit_loop, daemon=True)
         self._loop_thread = threading.Thread(target=self._loop, daemon=True)
         self._retire_thread = threading.Thread(target=self._retire_loop, daemon=True)
@@ -176,7 +183,8 @@ class Server:
                 self._admitted += 1
             try:
                 with torch.cuda.stream(self.encode_stream):
-                    req.tensor = alto_encode(req.coords, req.vals, req.dims, stream=self.encode_stream)
+                    coords, vals = self._stage_upload(req.coords, req.vals)
+                    req.tensor = alto_encode(coords, vals, req.dims, stream=self.encode_stream)
                     Batch.prepare(req.tensor, req.R)  # its waits stay off the loop thread
                     # initial factors on the encode stream (the batch orders
                     # itself after the handle's stream)
@@ -195,6 +203,20 @@ class Server:
                     self._admitted -= 1
                     self.errors += 1
                 req.future.set_exception(e)
+
+    def _stage_upload(self, coords: np.ndarray, vals: np.ndarray):
+        """The request's COO arrays copied into the pinned upload buffer
+        (alto_encode copies them in and waits, so the buffer is free again
+        when it returns); arrays that do not fit go as they are."""
+        cb = coords.size * 4
+        vb = vals.size * 4
+        if cb + vb > self._up.size:
+            return coords, vals
+        c = self._up[:cb].view(np.uint32).reshape(coords.shape)
+        v = self._up[cb:cb + vb].view(np.float32)
+        np.copyto(c, coords, casting="unsafe")
+        np.copyto(v, vals, casting="unsafe")
+        return c, v
 
     def _can_admit(self) -> bool:
         if not self._waiting or self._admitted >= self.max_slots:
@@ -224,9 +246,14 @@ class Server:
                 gone = self._to_remove
                 self._to_remove = []
             for slot, req in gone:
+                t_r = time.perf_counter()
                 self.batch.remove(slot)
+                t_f = time.perf_counter()
                 req.tensor.free()
                 req.tensor = None
+                self.loop_s["remove"] += t_f - t_r
+                self.loop_s["free"] += time.perf_counter() - t_f
+            t_ba = time.perf_counter()
             for req in ready:
                 try:
                     slot = self.batch.add(req.tensor, req.R, req.iters, req.init, tol=req.tol)
@@ -235,6 +262,7 @@ class Server:
                     self._finish_error(req, e)
             t_b = time.perf_counter()
             self.loop_s["add"] += t_b - t_a
+            self.loop_s["batch_add"] += t_b - t_ba
             if self._live:
                 self.batch.step(self.steps_per_round)
                 done = self.batch.poll(wait=False)
@@ -269,11 +297,9 @@ class Server:
                 item = self._retiring.pop(0)
             t0 = time.perf_counter()
             slot, req, iters_done, status = item
-            res_f = [np.empty((d, req.R), dtype=np.float32) for d in req.dims]
-            lam_h = np.empty(req.R)
-            fits_h = np.zeros(req.iters)
-            self.batch.copy_out(slot, res_f, lam_h, fits_h, stream=self.retire_stream)
+            res_f = self._download(slot, req)
             now = time.perf_counter()
+            res_f, lam_h, fits_h = res_f
             res = CPResult(res_f, lam_h, fits_h[:iters_done].tolist(), iters_done, status, req.arrival,
                            req.admitted, now)
             with self._lock:
@@ -287,6 +313,42 @@ class Server:
                 self.loop_s["retire_finish"] += now - t0
                 self._lock.notify_all()
             req.future.set_result(res)
+
+    def _download(self, slot: int, req: _Request):
+        """The slot's factors, lambda and fits through the pinned download
+        buffer (one factor at a time when they do not fit together)."""
+        N = len(req.dims)
+        sizes = [d * req.R * 4 for d in req.dims]
+        small = 8 * req.R + 8 * req.iters
+        lam_h = np.empty(req.R)
+        fits_h = np.zeros(req.iters)
+        out = [np.empty((d, req.R), dtype=np.float32) for d in req.dims]
+        if sum(sizes) + small <= self._down.size:
+            offs = np.cumsum([0] + sizes)
+            bufs = [self._down[offs[m]:offs[m + 1]].view(np.float32) for m in range(N)]
+            lb = self._down[offs[N]:offs[N] + 8 * req.R].view(np.float64)
+            fb = self._down[offs[N] + 8 * req.R:offs[N] + small].view(np.float64)
+            self.batch.copy_out(slot, bufs, lb, fb, stream=self.retire_stream)
+            for m in range(N):
+                np.copyto(out[m].reshape(-1), bufs[m])
+            np.copyto(lam_h, lb)
+            np.copyto(fits_h, fb)
+        else:
+            for m in range(N):
+                if sizes[m] <= self._down.size:
+                    buf = self._down[:sizes[m]].view(np.float32)
+                    self.batch.copy_out(slot, [buf if k == m else None for k in range(N)],
+                                        stream=self.retire_stream)
+                    np.copyto(out[m].reshape(-1), buf)
+                else:
+                    self.batch.copy_out(slot, [out[m] if k == m else None for k in range(N)],
+                                        stream=self.retire_stream)
+            lb = self._down[:8 * req.R].view(np.float64)
+            fb = self._down[8 * req.R:small].view(np.float64)
+            self.batch.copy_out(slot, [None] * N, lb, fb, stream=self.retire_stream)
+            np.copyto(lam_h, lb)
+            np.copyto(fits_h, fb)
+        return out, lam_h, fits_h
 
     def _finish_error(self, req: _Request, e: Exception) -> None:
         if req.tensor is not None:
@@ -310,6 +372,9 @@ def run_fcfs(requests, schedule_start: float) -> dict:
     lat, work = [], 0.0
     not_spd = 0
     t_first = t_last = None
+    # the same pinned staging the Server uses
+    up = torch.empty(256 << 20, dtype=torch.uint8, pin_memory=True).numpy()
+    down = torch.empty(256 << 20, dtype=torch.uint8, pin_memory=True)
     for arrival_off, coords, vals, dims, R, iters, init, seed in requests:
         arrival = schedule_start + arrival_off
         now = time.perf_counter()
@@ -317,7 +382,15 @@ def run_fcfs(requests, schedule_start: float) -> dict:
             time.sleep(arrival - now)
         if t_first is None:
             t_first = arrival
-        t = alto_encode(coords, vals, dims)
+        cb, vb = coords.size * 4, vals.size * 4
+        if cb + vb <= up.size:
+            c = up[:cb].view(np.uint32).reshape(coords.shape)
+            v = up[cb:cb + vb].view(np.float32)
+            np.copyto(c, coords, casting="unsafe")
+            np.copyto(v, vals, casting="unsafe")
+            t = alto_encode(c, v, dims)
+        else:
+            t = alto_encode(coords, vals, dims)
         if init is None:
             A = device_factors(dims, R, seed)
         else:
@@ -329,7 +402,15 @@ def run_fcfs(requests, schedule_start: float) -> dict:
                 raise
             not_spd += 1
             fits = []
-        outs = [a.cpu().numpy() for a in A]  # results on the host, as the Server delivers them
+        outs = []  # results on the host, through pinned staging as the Server does
+        for a in A:
+            n = a.numel()
+            if n * 4 <= down.numel():
+                buf = down[: n * 4].view(torch.float32)
+                buf.copy_(a.reshape(-1))
+                outs.append(buf.numpy().reshape(a.shape).copy())
+            else:
+                outs.append(a.cpu().numpy())
         t.free()
         t_last = time.perf_counter()
         lat.append(t_last - arrival)
