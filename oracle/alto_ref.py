@@ -29,6 +29,11 @@ Readings of the paper that this file fixes (each also listed in the design doc):
   ||X||^2 + lambda^T (*_m G_m) lambda - 2 <X, X_hat>.
 * Duplicate coordinates are separate COO entries that add up into one cell of
   X: MTTKRP sums them term by term, and ||X||^2 squares the summed cells.
+* pos_out of Alg. 4 (the output-oriented traversal) lists, segment by
+  segment, the ordered positions of the segment by increasing coordinate of
+  the output mode; equal coordinates keep line order. Segments are those of
+  Section IV-A for a given L. A row is a boundary row of a segment when
+  another segment also has nonzeros in it: only those updates need atomics.
 """
 from __future__ import annotations
 
@@ -266,6 +271,71 @@ def mttkrp(coords: np.ndarray, vals: np.ndarray, factors: Sequence[np.ndarray],
                 t = t * np.asarray(factors[m], dtype=np.float64)[coords[m, a:b].astype(np.int64)]
         np.add.at(out, coords[mode, a:b].astype(np.int64), t)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Alg. 4, output-oriented branch: the stored order pos_out and the traversal
+# ---------------------------------------------------------------------------
+
+def pos_out(t: AltoTensor, L: int, mode: int) -> np.ndarray:
+    """Ordered positions [M] (int64): inside every line segment l of L
+    (Section IV-A), the segment's positions by increasing coordinate of
+    `mode`, ties in line order (a stable sort per segment)."""
+    M = t.nnz
+    coords = delinearize(t.lo, t.hi, t.plan)
+    starts = segment_starts(M, L)
+    out = np.empty(M, dtype=np.int64)
+    for l in range(L):
+        a, b = int(starts[l]), int(starts[l + 1])
+        out[a:b] = a + np.argsort(coords[mode, a:b], kind="stable")
+    return out
+
+
+def mttkrp_output_oriented(t: AltoTensor, factors: Sequence[np.ndarray], mode: int,
+                           L: int) -> Tuple[np.ndarray, int, int]:
+    """Alg. 4 with output-oriented traversal, segments taken one after the
+    other: each segment visits its nonzeros in pos_out order, sums the
+    contribution v * prod_{m != mode} A_m(i_m, :) of consecutive nonzeros with
+    the same output row, and adds the sum to the output when the row changes
+    (or the segment ends). Returns (M fp64, number of row updates, number of
+    those updates that go to a boundary row, i.e. a row that another segment
+    also updates)."""
+    N = len(factors)
+    R = factors[0].shape[1]
+    out = np.zeros((factors[mode].shape[0], R), dtype=np.float64)
+    coords = delinearize(t.lo, t.hi, t.plan)
+    order = pos_out(t, L, mode)
+    starts = segment_starts(t.nnz, L)
+    F = [np.asarray(A, dtype=np.float64) for A in factors]
+    owners = {}
+    for l in range(L):
+        a, b = int(starts[l]), int(starts[l + 1])
+        for i in set(coords[mode, a:b].tolist()):
+            owners[i] = owners.get(i, 0) + 1
+    updates = boundary = 0
+    for l in range(L):
+        a, b = int(starts[l]), int(starts[l + 1])
+        row, acc = None, None
+        for k in range(a, b):
+            x = int(order[k])
+            i = int(coords[mode, x])
+            term = float(t.vals[x]) * np.ones(R)
+            for m in range(N):
+                if m != mode:
+                    term = term * F[m][int(coords[m, x])]
+            if i != row:
+                if row is not None:
+                    out[row] += acc
+                    updates += 1
+                    boundary += owners[row] > 1
+                row, acc = i, term
+            else:
+                acc = acc + term
+        if row is not None:
+            out[row] += acc
+            updates += 1
+            boundary += owners[row] > 1
+    return out, updates, boundary
 
 
 def to_dense(coords: np.ndarray, vals: np.ndarray, dims: Sequence[int]) -> np.ndarray:
