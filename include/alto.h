@@ -55,18 +55,27 @@ typedef enum alto_dtype { ALTO_F32 = 0, ALTO_BF16 = 1 } alto_dtype;
  *          summed in registers; the most reused rows of the mode ("hot rows",
  *          picked at encode time) are staged in shared memory per line
  *          segment and flushed once per segment; all other rows are added to
- *          the output with vector atomics (the output-oriented branch).
+ *          the output with vector atomics (the atomic updates of the
+ *          output-oriented branch, without its stored order).
  *  PULL:   each line segment accumulates into a shared-memory Temp over its
  *          mode interval [T^s, T^e], writes it out as a partial, and a second
  *          kernel pulls, for each output row, the partials of the segments
  *          whose interval contains it (the recursive branch).
+ *  OUTPUT: the output-oriented traversal through the stored order pos_out
+ *          of the mode (alto_build_pos_out; built on first use with the
+ *          current segment count when missing): nonzeros of one output row
+ *          are consecutive in it, each group of threads walks a contiguous
+ *          piece of it, sums each run of equal row in registers across the
+ *          whole piece and adds the run to the output with one vector atomic.
+ *          Costs 4 bytes per nonzero for the mode's stored order.
  *  AUTO:   PULL when the fiber reuse nnz/dims[mode] exceeds 4 (the paper's
  *          cost of buffered accumulation) and the largest interval fits in
- *          shared memory, else ATOMIC. */
+ *          shared memory, else ATOMIC (never OUTPUT, which needs memory). */
 typedef enum alto_variant {
   ALTO_VARIANT_AUTO = 0,
   ALTO_VARIANT_ATOMIC = 1,
-  ALTO_VARIANT_PULL = 2
+  ALTO_VARIANT_PULL = 2,
+  ALTO_VARIANT_OUTPUT = 3
 } alto_variant;
 
 /* Optional device-memory allocator. alloc returns a device pointer aligned to
@@ -106,7 +115,8 @@ typedef struct alto_mode_plan {
                          nonzero over R/cols_per_lane threads ("threads per
                          nonzero"); cols_per_lane == R (R >= 8) gives each
                          nonzero one thread, which walks its rows in 8-column
-                         chunks; 0 = library default                            */
+                         chunks; 0 = library default. OUTPUT uses 4 or 8
+                         (larger requests take 8, or 4 when R = 4)               */
   int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit             */
 } alto_mode_plan;
 
@@ -175,6 +185,37 @@ alto_status alto_copy_hot_rows(alto_handle_t h, int mode, uint32_t *rows, uint32
  * for rank R into the concrete choice the next alto_mttkrp would make. */
 alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *plan);
 alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan *plan);
+
+/* ---------------------------------------------------------------------------
+ * alto_build_pos_out -- the stored order of Alg. 4's output-oriented
+ * traversal (pos_out) for one mode, or every mode with mode = -1: inside
+ * every line segment l of nparts, [floor(l*nnz/nparts),
+ * floor((l+1)*nnz/nparts)) as in Section IV-A, the segment's ordered
+ * positions by increasing coordinate of the mode; equal coordinates keep line
+ * order. Kept in the handle as nnz uint32 positions per mode (4 bytes per
+ * nonzero per mode: the paper keeps one tensor copy, the order costs this
+ * much on top), replacing an earlier order of that mode, until
+ * alto_free_pos_out or alto_free. The ALTO_VARIANT_OUTPUT plan walks it.
+ *
+ *  nparts  segments of the order; 0 = the handle's current segment count,
+ *          values above nnz count as nnz. Later alto_set_partitions calls do
+ *          not change a stored order.
+ * Built on the device by one stable radix sort of (segment, coordinate) keys
+ * (scratch of about 28 bytes per nonzero while it runs). Asynchronous.
+ * Errors: INVALID_ARG (mode), UNSUPPORTED (nnz >= 2^32 - 512), OOM, CUDA.
+ * ------------------------------------------------------------------------- */
+alto_status alto_build_pos_out(alto_handle_t h, int mode, uint64_t nparts, void *stream);
+
+/* Copy the stored order of `mode` (nnz uint32 ordered positions) to dst, host
+ * or device memory; synchronises the stream when dst is host memory.
+ * *nparts (may be NULL) receives its segment count. Errors: INVALID_ARG
+ * (mode, NULL dst, no order stored for the mode), CUDA. */
+alto_status alto_copy_pos_out(alto_handle_t h, int mode, uint32_t *dst, uint64_t *nparts,
+                              void *stream);
+
+/* Release the stored order of `mode` (-1: every mode). Modes whose plan is
+ * OUTPUT build it again on their next MTTKRP. */
+alto_status alto_free_pos_out(alto_handle_t h, int mode);
 
 /* ---------------------------------------------------------------------------
  * alto_mttkrp -- M = X_(mode) (A^(1) (.) ... A^(mode-1) (.) A^(mode+1) ... (.) A^(N))
@@ -275,12 +316,17 @@ alto_status alto_mttkrp_grouped(int n, const alto_handle_t *hs, const int *modes
  *
  *  factors  as in alto_mttkrp (all modes set; device, 16-byte aligned).
  *  out      device scratch of max_n I_n x R floats (overwritten).
- *  flags    0 or ALTO_TUNE_SEGMENTS.
+ *  flags    0, or ALTO_TUNE_SEGMENTS and / or ALTO_TUNE_OUTPUT. With
+ *           ALTO_TUNE_OUTPUT the OUTPUT plan (4 and 8 columns per lane) joins
+ *           the candidates at the original segment count: each mode's order
+ *           is built with that count; a mode keeps its order only if OUTPUT
+ *           wins there.
  *  res      the chosen plan (resolved), its time and the default plan's time
  *           per mode, the segment count, and the number of timed candidates.
  * Synchronises the stream. Errors: those of alto_mttkrp.
  * ------------------------------------------------------------------------- */
 #define ALTO_TUNE_SEGMENTS 1
+#define ALTO_TUNE_OUTPUT 2
 
 typedef struct alto_tune_result {
   alto_mode_plan plan[ALTO_MAX_MODES];

@@ -24,7 +24,7 @@ LIB_PATH = os.environ.get("ALTO_LIB") or os.path.join(_PKG, "_build", "libalto.s
 ALTO_MAX_MODES = 8
 ALTO_MAX_HOT = 4096
 ALTO_F32, ALTO_BF16 = 0, 1
-VARIANT_AUTO, VARIANT_ATOMIC, VARIANT_PULL = 0, 1, 2
+VARIANT_AUTO, VARIANT_ATOMIC, VARIANT_PULL, VARIANT_OUTPUT = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "ALTO_OK", -1: "ALTO_ERR_INVALID_ARG", -2: "ALTO_ERR_OOM", -3: "ALTO_ERR_CUDA",
                 -4: "ALTO_ERR_UNSUPPORTED", -5: "ALTO_ERR_COORD_RANGE", -6: "ALTO_ERR_NOT_SPD",
@@ -76,6 +76,7 @@ class alto_tune_result(ctypes.Structure):
 
 
 ALTO_TUNE_SEGMENTS = 1
+ALTO_TUNE_OUTPUT = 2
 
 
 class alto_apr_params(ctypes.Structure):
@@ -111,6 +112,9 @@ SIGNATURES = {
     "alto_copy_hot_rows": ([_vp, _i32, _vp, _u32, ctypes.POINTER(_u32)], _i32),
     "alto_set_mode_plan": ([_vp, _i32, ctypes.POINTER(alto_mode_plan)], _i32),
     "alto_get_mode_plan": ([_vp, _i32, _i32, ctypes.POINTER(alto_mode_plan)], _i32),
+    "alto_build_pos_out": ([_vp, _i32, _u64, _vp], _i32),
+    "alto_copy_pos_out": ([_vp, _i32, _vp, ctypes.POINTER(_u64), _vp], _i32),
+    "alto_free_pos_out": ([_vp, _i32], _i32),
     "alto_mttkrp": ([_vp, _i32, _vp, _i32, _i32, _vp, _vp], _i32),
     "cpals_run": ([_vp, _i32, _i32, _vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(_i32), _vp],
                   _i32),
@@ -475,10 +479,26 @@ class AltoTensor:
         alto_mttkrp(self, mode, factors, R, out, code, stream)
         return out
 
+    def build_pos_out(self, mode: int = -1, nparts: int = 0, stream=None) -> None:
+        """alto_build_pos_out: the stored output-oriented order of one mode (-1: all)."""
+        _check(lib().alto_build_pos_out(self.handle, int(mode), int(nparts), _stream_ptr(stream)))
+
+    def pos_out(self, mode: int, stream=None) -> Tuple[np.ndarray, int]:
+        """alto_copy_pos_out: (the stored order of `mode` as uint32 positions, its segment count)."""
+        buf = np.empty(max(self.nnz, 1), dtype=np.uint32)
+        L = ctypes.c_uint64(0)
+        _check(lib().alto_copy_pos_out(self.handle, int(mode), buf.ctypes.data, ctypes.byref(L),
+                                       _stream_ptr(stream)))
+        return buf[: self.nnz], int(L.value)
+
+    def free_pos_out(self, mode: int = -1) -> None:
+        _check(lib().alto_free_pos_out(self.handle, int(mode)))
+
     def autotune(self, factors, R: int, out=None, segments: bool = True, dtype=None,
-                 stream=None) -> dict:
+                 stream=None, output: bool = False) -> dict:
         """alto_autotune: measured per-mode plan (and segment count); the
-        winners stay set on the handle. Returns the report as a dict."""
+        winners stay set on the handle. ``output`` adds the OUTPUT plan (the
+        stored order) to the candidates. Returns the report as a dict."""
         torch = _torch()
         code = ALTO_F32
         if dtype is not None:
@@ -490,7 +510,8 @@ class AltoTensor:
         arr = (ctypes.c_void_p * self.nmodes)(*[_ptr(f) for f in factors])
         res = alto_tune_result()
         _check(lib().alto_autotune(self.handle, int(R), arr, int(code), _ptr(out),
-                                   ALTO_TUNE_SEGMENTS if segments else 0, _stream_ptr(stream),
+                                   (ALTO_TUNE_SEGMENTS if segments else 0)
+                                   | (ALTO_TUNE_OUTPUT if output else 0), _stream_ptr(stream),
                                    ctypes.byref(res)))
         n = self.nmodes
         return {"plans": [(int(res.plan[i].variant), int(res.plan[i].cols_per_lane),

@@ -414,6 +414,12 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   // one thread per nonzero needs R >= 8 (8-column chunks)
   if (p.cols_per_lane == R && R < 8) p.cols_per_lane = 4;
   if (p.cols_per_lane > 16 && p.cols_per_lane != R) p.cols_per_lane = 16;
+  if (p.variant == ALTO_VARIANT_OUTPUT) {
+    p.cols_per_lane = (p.cols_per_lane >= 8 && R >= 8) ? 8 : 4;
+    p.hot_rows = 0;
+    *out = p;
+    return ALTO_OK;
+  }
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
   const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
@@ -433,6 +439,25 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   }
   *out = p;
   return ALTO_OK;
+}
+
+// Builds (or rebuilds) the stored order of mode n with L segments (0 = the
+// current count) and keeps it in the handle.
+alto_status set_pos_out(alto_tensor *h, int n, uint64_t L, cudaStream_t s) {
+  if (L == 0) L = h->L;
+  uint32_t *po = nullptr;
+  alto_status st = build_pos_out(h, n, L, &po, s);
+  if (st != ALTO_OK) return st;
+  dfree(h, h->pos_out[n], std::max<uint64_t>(h->M, 1) * 4, s);
+  h->pos_out[n] = po;
+  h->pos_out_L[n] = h->M ? std::min<uint64_t>(std::max<uint64_t>(L, 1), h->M) : 1;
+  return ALTO_OK;
+}
+
+void free_pos_out(alto_tensor *h, int n, cudaStream_t s) {
+  dfree(h, h->pos_out[n], std::max<uint64_t>(h->M, 1) * 4, s);
+  h->pos_out[n] = nullptr;
+  h->pos_out_L[n] = 0;
 }
 
 alto_status check_handle(alto_tensor *h) {
@@ -475,6 +500,20 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
   }
   if (h->M == 0) {
     CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
+    return ALTO_OK;
+  }
+  if (p.variant == ALTO_VARIANT_OUTPUT) {
+    if (!h->pos_out[mode] && (st = set_pos_out(h, mode, 0, s)) != ALTO_OK) return st;
+    if (p.cols_per_lane == 8 && !bf16)
+      for (int m = 0; m < h->N; ++m)
+        if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
+    a.perm = h->pos_out[mode];
+    {
+      ProfScope ps(h, ALTO_PROF_ZERO, s);
+      CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
+    }
+    ProfScope ps(h, ALTO_PROF_MTTKRP, s);
+    CUDA_TRY(launch_mttkrp_out(a, p.cols_per_lane, bf16, h->num_sms, s));
     return ALTO_OK;
   }
   if (p.variant == ALTO_VARIANT_PULL) {
@@ -539,6 +578,10 @@ alto_status phi_impl(alto_tensor *h, int mode, const float *const *A, const floa
   alto_mode_plan p;
   alto_status st = resolve_plan(h, mode, R, &p);
   if (st != ALTO_OK) return st;
+  if (p.variant == ALTO_VARIANT_OUTPUT) {  // Phi has no stored-order kernel: ATOMIC
+    p.variant = ALTO_VARIANT_ATOMIC;
+    p.hot_rows = hot_slots_that_fit(R, (int)h->nhot[mode]);
+  }
   MttkrpArgs a{};
   a.bp = h->bp;
   a.bp.out_rank = h->rank_of[mode];
@@ -836,6 +879,7 @@ void alto_free(alto_handle_t h) {
   for (int n = 0; n < kMaxModes; ++n) {
     free_pull(h, n, s);
     free_hot(h, n, s);
+    free_pos_out(h, n, s);
     for (HotTable &t : h->group_hot[n])
       if (t.htab) dfree(h, t.htab, ((size_t)1 << t.hbits) * sizeof(uint64_t), s);
     if (h->hot_rows[n]) dfree(h, h->hot_rows[n], ALTO_MAX_HOT * 4, s);
@@ -978,7 +1022,7 @@ alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *
   alto_status st = check_handle(h);
   if (st != ALTO_OK) return st;
   if (mode < 0 || mode >= h->N || !plan) return fail(ALTO_ERR_INVALID_ARG, "bad mode or plan");
-  if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_PULL)
+  if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_OUTPUT)
     return fail(ALTO_ERR_INVALID_ARG, "unknown variant %d", plan->variant);
   if (plan->cols_per_lane != 0 && plan->cols_per_lane != 4 && plan->cols_per_lane != 8 &&
       plan->cols_per_lane != 16 && plan->cols_per_lane != 32 && plan->cols_per_lane != 64)
@@ -993,6 +1037,42 @@ alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan 
   if (mode < 0 || mode >= h->N || !plan) return fail(ALTO_ERR_INVALID_ARG, "bad mode or plan");
   if (!rank_ok(R)) return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
   return resolve_plan(h, mode, R, plan);
+}
+
+alto_status alto_build_pos_out(alto_handle_t h, int mode, uint64_t nparts, void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < -1 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "bad mode %d", mode);
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  for (int n = 0; n < h->N; ++n)
+    if (mode < 0 || n == mode)
+      if ((st = set_pos_out(h, n, nparts, s)) != ALTO_OK) return st;
+  return ALTO_OK;
+}
+
+alto_status alto_copy_pos_out(alto_handle_t h, int mode, uint32_t *dst, uint64_t *nparts,
+                              void *stream) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < 0 || mode >= h->N || !dst) return fail(ALTO_ERR_INVALID_ARG, "bad mode or dst");
+  if (!h->pos_out[mode]) return fail(ALTO_ERR_INVALID_ARG, "no stored order for mode %d", mode);
+  cudaStream_t s = (cudaStream_t)stream;
+  h->stream = s;
+  if (nparts) *nparts = h->pos_out_L[mode];
+  if (h->M == 0) return ALTO_OK;
+  CUDA_TRY(cudaMemcpyAsync(dst, h->pos_out[mode], h->M * 4, cudaMemcpyDefault, s));
+  if (!is_device_ptr(dst)) CUDA_TRY(cudaStreamSynchronize(s));
+  return ALTO_OK;
+}
+
+alto_status alto_free_pos_out(alto_handle_t h, int mode) {
+  alto_status st = check_handle(h);
+  if (st != ALTO_OK) return st;
+  if (mode < -1 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "bad mode %d", mode);
+  for (int n = 0; n < h->N; ++n)
+    if (mode < 0 || n == mode) free_pos_out(h, n, h->stream);
+  return ALTO_OK;
 }
 
 alto_status alto_mttkrp(alto_handle_t h, int mode, const void *const *factors, alto_dtype fdtype,
@@ -1227,6 +1307,8 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
     return ALTO_OK;
   };
   const uint64_t L0 = h->L;
+  bool had_pos_out[kMaxModes] = {};
+  for (int n = 0; n < N; ++n) had_pos_out[n] = h->pos_out[n] != nullptr;
   std::vector<uint64_t> Ls{L0};
   if (flags & ALTO_TUNE_SEGMENTS) {
     for (uint64_t seg : {4096ull, 16384ull, 65536ull}) {
@@ -1253,6 +1335,9 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
       if (pull_smem <= mttkrp_smem_limit())
         for (int c : cpls)
           if (R % c == 0 && c < R) cands.push_back(alto_mode_plan{ALTO_VARIANT_PULL, c, -1});
+      if ((flags & ALTO_TUNE_OUTPUT) && L == L0)
+        for (int c : cpls)
+          if (R % c == 0 && (c == 4 || R >= 8)) cands.push_back(alto_mode_plan{ALTO_VARIANT_OUTPUT, c, 0});
       if (cands.empty()) cands.push_back(alto_mode_plan{ALTO_VARIANT_AUTO, 0, -1});
       double bms = 1e300;
       alto_mode_plan bp{};
@@ -1286,6 +1371,8 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
   }
   if (h->L != best_L && (st = run_partition(h, best_L, s)) != ALTO_OK) return done(st);
   for (int n = 0; n < N; ++n) {
+    // an order the tuning built is kept only where OUTPUT won
+    if (!had_pos_out[n] && best_plan[n].variant != ALTO_VARIANT_OUTPUT) free_pos_out(h, n, s);
     h->plan[n] = best_plan[n];
     resolve_plan(h, n, R, &res->plan[n]);
     res->ms[n] = best_ms[n];

@@ -65,6 +65,12 @@ alto_status repartition(alto_tensor *h, uint64_t L, cudaStream_t s);
 alto_status ensure_group_hot(alto_tensor *h, int n, int nslots, cudaStream_t s,
                              const HotTable **out);
 
+// pos_out of Alg. 4 for one mode: inside every segment l of L, the ordered
+// positions by increasing coordinate of `mode`, ties in line order, as nnz
+// uint32 positions in *out (needs nnz < 2^32). Scratch and result come from
+// the handle's allocator; the result is the caller's (4 * nnz bytes).
+alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, cudaStream_t s);
+
 }  // namespace alto
 
 struct alto_tensor {
@@ -115,6 +121,8 @@ struct alto_tensor {
   HotTable group_hot[alto::kMaxModes][5];  // smaller tables for grouped launches, by size
   PullPlan pull[alto::kMaxModes];
   Buf partials;
+  uint32_t *pos_out[alto::kMaxModes] = {};  // stored output-oriented order per mode
+  uint64_t pos_out_L[alto::kMaxModes] = {}; // its segment count
   // instrumentation
   bool prof_on = false;
   std::vector<ProfEvt> prof_pending;

@@ -46,6 +46,8 @@ struct MttkrpArgs {
   const float *pimat;          // precomputed Pi [nnz][R] (PRE) or null (OTF)
   float eps;
   const int *skip;             // nonzero: return at once (inner loop converged)
+  // output-oriented traversal (Alg. 4): pos_out of the output mode [nnz]
+  const uint32_t *perm;
 };
 
 // Shared memory the segment kernel needs.
@@ -73,6 +75,12 @@ cudaError_t launch_pull_reduce(const float *partials, const uint64_t *row_ptr, c
 // Phi (Alg. 5) for a.mode: a.bmat set, a.pimat set for PRE.
 cudaError_t launch_phi(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
                        cudaStream_t s);
+
+// MTTKRP walking a.perm (the stored output-oriented order of a.mode).
+cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s);
+
+template <int NT>
+cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s);
 
 template <int NT>
 cudaError_t launch_phi_nt(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,

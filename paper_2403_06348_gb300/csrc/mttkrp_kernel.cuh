@@ -194,6 +194,62 @@ __device__ __forceinline__ void decode_blocks(const BlockPlan &bp, uint64_t lo, 
   if constexpr (Q + 1 < N) decode_blocks<KW, N, Q + 1>(bp, lo, hi, c);
 }
 
+// p = vj * (the product over the N-1 input factors of row ij[k]), this lane's
+// CPL columns of it. fb[k] is input factor k plus the lane's byte offset.
+template <int NMAX, int CPL, bool BF16>
+__device__ __forceinline__ void gather_product(const char *const (&fb)[NMAX > 1 ? NMAX - 1 : 1],
+                                               const uint32_t (&ij)[NMAX > 1 ? NMAX - 1 : 1],
+                                               uint32_t rowb, int tpn, int N, float vj,
+                                               float (&p)[CPL]) {
+  constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) {
+    if (k + 1 < N) {
+      const char *rb = fb[k] + (uint64_t)ij[k] * rowb;
+      float f[CPL];
+      if constexpr (CPL == 8 && !BF16) {
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]),
+              "=f"(f[7])
+            : "l"(rb));
+      } else if constexpr (CPL == 8) {
+        const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(rb));
+        f[0] = bf16lo(qv.x);
+        f[1] = bf16hi(qv.x);
+        f[2] = bf16lo(qv.y);
+        f[3] = bf16hi(qv.y);
+        f[4] = bf16lo(qv.z);
+        f[5] = bf16hi(qv.z);
+        f[6] = bf16lo(qv.w);
+        f[7] = bf16hi(qv.w);
+      } else {
+#pragma unroll
+      for (int w = 0; w < CPL / 4; ++w) {
+        const int voff = w * tpn * (BF16 ? 8 : 16);
+        if constexpr (!BF16) {
+          const float4 qv = __ldg(reinterpret_cast<const float4 *>(rb + voff));
+          f[4 * w] = qv.x;
+          f[4 * w + 1] = qv.y;
+          f[4 * w + 2] = qv.z;
+          f[4 * w + 3] = qv.w;
+        } else {
+          const uint2 qv = __ldg(reinterpret_cast<const uint2 *>(rb + voff));
+          f[4 * w] = bf16lo(qv.x);
+          f[4 * w + 1] = bf16hi(qv.x);
+          f[4 * w + 2] = bf16lo(qv.y);
+          f[4 * w + 3] = bf16hi(qv.y);
+        }
+      }
+      }
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) p[c] = (k == 0 ? vj : p[c]) * f[c];
+    } else if (k == 0) {
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) p[c] = vj;
+    }
+  }
+}
+
 #ifndef ALTO_MTTKRP_RUNS
 #define ALTO_MTTKRP_RUNS 1
 #endif
@@ -274,53 +330,8 @@ __device__ __forceinline__ void group_rounds(const char *const (&fb)[NMAX > 1 ? 
 #pragma unroll
       for (int c = 0; c < 4; ++c) p[c] = scale * kr[c];
     } else {
-    if (TAIL && j >= nvalid) continue;
-#pragma unroll
-    for (int k = 0; k < NIN; ++k) {
-      if (k + 1 < N) {
-        const char *rb = fb[k] + (uint64_t)ij[k] * rowb;
-        float f[CPL];
-        if constexpr (CPL == 8 && !BF16) {
-          asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-              : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]), "=f"(f[6]),
-                "=f"(f[7])
-              : "l"(rb));
-        } else if constexpr (CPL == 8) {
-          const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(rb));
-          f[0] = bf16lo(qv.x);
-          f[1] = bf16hi(qv.x);
-          f[2] = bf16lo(qv.y);
-          f[3] = bf16hi(qv.y);
-          f[4] = bf16lo(qv.z);
-          f[5] = bf16hi(qv.z);
-          f[6] = bf16lo(qv.w);
-          f[7] = bf16hi(qv.w);
-        } else {
-#pragma unroll
-        for (int w = 0; w < CPL / 4; ++w) {
-          const int voff = w * tpn * (BF16 ? 8 : 16);
-          if constexpr (!BF16) {
-            const float4 qv = __ldg(reinterpret_cast<const float4 *>(rb + voff));
-            f[4 * w] = qv.x;
-            f[4 * w + 1] = qv.y;
-            f[4 * w + 2] = qv.z;
-            f[4 * w + 3] = qv.w;
-          } else {
-            const uint2 qv = __ldg(reinterpret_cast<const uint2 *>(rb + voff));
-            f[4 * w] = bf16lo(qv.x);
-            f[4 * w + 1] = bf16hi(qv.x);
-            f[4 * w + 2] = bf16lo(qv.y);
-            f[4 * w + 3] = bf16hi(qv.y);
-          }
-        }
-        }
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) p[c] = (k == 0 ? vj : p[c]) * f[c];
-      } else if (k == 0) {
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) p[c] = vj;
-      }
-    }
+      if (TAIL && j >= nvalid) continue;
+      gather_product<NMAX, CPL, BF16>(fb, ij, rowb, tpn, N, vj, p);
     }
     if (ALTO_MTTKRP_RUNS && rj == run_row) {
 #pragma unroll

@@ -1,0 +1,6 @@
+// Output-oriented MTTKRP kernels specialised for 5 modes.
+#include "outorder.cuh"
+
+namespace alto {
+template cudaError_t launch_mttkrp_out_nt<5>(const MttkrpArgs &, int, bool, int, cudaStream_t);
+}  // namespace alto

@@ -1,0 +1,6 @@
+// Output-oriented MTTKRP kernels for any number of modes (decided at run time).
+#include "outorder.cuh"
+
+namespace alto {
+template cudaError_t launch_mttkrp_out_nt<0>(const MttkrpArgs &, int, bool, int, cudaStream_t);
+}  // namespace alto

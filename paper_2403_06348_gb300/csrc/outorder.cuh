@@ -1,0 +1,155 @@
+// MTTKRP with output-oriented traversal (Alg. 4, the pos_out branch),
+// included by the per-mode-count instantiation units out_n*.cu.
+//
+// The stored order pos_out lists, segment by segment, the ordered positions by
+// increasing output coordinate, so nonzeros of one output row sit next to each
+// other in it. Warps take chunks of 32 * kOutBatches consecutive entries of
+// pos_out; inside a chunk, each group of tpn = R / CPL lanes owns a contiguous
+// piece of tpn * kOutBatches entries and walks it in kOutBatches batches of
+// tpn nonzeros. The run of equal output row is carried in registers across
+// the batches of the piece and leaves with one vector atomic per run (the
+// paper's boundary update), so the number of global updates is the number of
+// distinct rows per piece instead of the number of nonzeros. No shared memory.
+#pragma once
+
+#include "mttkrp_kernel.cuh"
+
+namespace alto {
+
+constexpr int kOutBatches = 16;
+// Largest nnz with a stored order: entries are 32-bit and a chunk may run up
+// to 32 * kOutBatches entries past the end.
+constexpr uint64_t kPosOutMaxNnz = 0xFFFFFFFFull - 32ull * kOutBatches;
+
+template <int NT, int KW, int CPL, bool BF16>
+__global__ void __launch_bounds__(kMttkrpThreads, mttkrp_min_blocks<CPL>())
+    mttkrp_out_kernel(const __grid_constant__ MttkrpArgs a) {
+  constexpr int NMAX = NT ? NT : kMaxModes;
+  constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
+  const int N = NT ? NT : a.dp.nmodes;
+  const int R = a.R;
+  const int tpn = R / CPL;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / tpn, sub = lane - grp * tpn;
+  const int ro = a.out_rank;
+  const unsigned full = 0xffffffffu;
+  const uint32_t rowb = (uint32_t)R * (BF16 ? 2u : 4u);
+  const uint32_t inb = lane_byte_offset<CPL, BF16>(sub);
+  const char *fb[NIN];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) fb[k] = static_cast<const char *>(a.fin[k]) + inb;
+
+  // 32-bit entry arithmetic: pos_out exists only for nnz <= kPosOutMaxNnz
+  const uint32_t nnz = (uint32_t)a.nnz;
+  const uint32_t warp_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  constexpr uint32_t chunk = 32u * kOutBatches;
+  const uint32_t nchunks = (nnz + chunk - 1) / chunk;
+  const uint32_t piece = (uint32_t)tpn * kOutBatches;
+
+  for (uint32_t ch = warp_id; ch < nchunks; ch += nwarps) {
+    // entry of pos_out this lane loads in batch b: p0 + b * tpn
+    const uint32_t p0 = ch * chunk + (uint32_t)grp * piece + (uint32_t)sub;
+    uint32_t idx_next = 0, idx_after = 0;
+    uint64_t nlo = 0, nhi = 0;
+    float nv = 0.f;
+    auto load_idx = [&](int b) -> uint32_t {
+      const uint32_t p = p0 + (uint32_t)(b * tpn);
+      return (b < kOutBatches && p < nnz) ? __ldcs(a.perm + p) : 0u;
+    };
+    auto load_nz = [&](int b, uint32_t x) {
+      const uint32_t p = p0 + (uint32_t)(b * tpn);
+      if (b < kOutBatches && p < nnz) {
+        if (KW == 1) {
+          nlo = __ldg(reinterpret_cast<const unsigned long long *>(a.keys) + x);
+        } else {
+          const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2 *>(a.keys) + x);
+          nlo = kk.x;
+          nhi = kk.y;
+        }
+        nv = __ldg(a.vals + x);
+      }
+    };
+    idx_next = load_idx(0);
+    idx_after = load_idx(1);
+    load_nz(0, idx_next);
+
+    float run[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) run[c] = 0.f;
+    uint32_t run_row = kEmptyRow;
+    for (int b = 0; b < kOutBatches; ++b) {
+      const bool valid = p0 + (uint32_t)(b * tpn) < nnz;
+      const uint64_t lo = nlo, hi = nhi;
+      const float v = nv;
+      // the next batch's nonzero and the entry after it are loaded while this one runs
+      const uint32_t x_next = idx_after;
+      idx_after = load_idx(b + 2);
+      load_nz(b + 1, x_next);
+      uint32_t c[NMAX];
+      if constexpr (NT > 0)
+        decode_blocks<KW, NMAX, 0>(a.bp, lo, hi, c);
+      else
+        decode_runs<KW, NMAX>(a.dp, N, lo, hi, c);
+      uint32_t row = c[0];
+      uint32_t in[NIN];
+#pragma unroll
+      for (int n = 1; n < NMAX; ++n)
+        if (n == ro) row = c[n];
+#pragma unroll
+      for (int k = 0; k < NIN; ++k) in[k] = (NMAX > 1 && k + 1 < NMAX) ? (k < ro ? c[k] : c[k + 1]) : 0u;
+      const unsigned live = __ballot_sync(full, valid);
+      if (!live) break;
+#pragma unroll(CPL <= 8 ? 2 : 1)
+      for (int q = 0; q < tpn; ++q) {
+        const int j = grp * tpn + q;
+        const float vj = __shfl_sync(full, v, j);
+        const uint32_t rj = __shfl_sync(full, row, j);
+        uint32_t ij[NIN];
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) ij[k] = (k + 1 < N) ? __shfl_sync(full, in[k], j) : 0u;
+        if (!((live >> j) & 1u)) continue;
+        float p[CPL];
+        gather_product<NMAX, CPL, BF16>(fb, ij, rowb, tpn, N, vj, p);
+        if (rj == run_row) {
+#pragma unroll
+          for (int cc = 0; cc < CPL; ++cc) run[cc] += p[cc];
+        } else {
+          if (run_row != kEmptyRow) flush_run<CPL, false>(run, run_row, -1, nullptr, a.out, R, sub, tpn, grp);
+#pragma unroll
+          for (int cc = 0; cc < CPL; ++cc) run[cc] = p[cc];
+          run_row = rj;
+        }
+      }
+    }
+    if (run_row != kEmptyRow) flush_run<CPL, false>(run, run_row, -1, nullptr, a.out, R, sub, tpn, grp);
+  }
+}
+
+template <int NT, int KW, int CPL, bool BF16>
+static cudaError_t launch_out_one(const MttkrpArgs &a, int num_sms, cudaStream_t s) {
+  auto kern = mttkrp_out_kernel<NT, KW, CPL, BF16>;
+  const uint64_t chunks = (a.nnz + 32ull * kOutBatches - 1) / (32ull * kOutBatches);
+  const uint64_t warps_per_cta = kMttkrpThreads / 32;
+  uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, 0);
+  const uint64_t need = (chunks + warps_per_cta - 1) / warps_per_cta;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, kMttkrpThreads, 0, s>>>(a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s) {
+  if (a.dp.kw == 1) {
+    if (cpl == 8) return bf16 ? launch_out_one<NT, 1, 8, true>(a, num_sms, s)
+                              : launch_out_one<NT, 1, 8, false>(a, num_sms, s);
+    return bf16 ? launch_out_one<NT, 1, 4, true>(a, num_sms, s) : launch_out_one<NT, 1, 4, false>(a, num_sms, s);
+  }
+  if (cpl == 8) return bf16 ? launch_out_one<NT, 2, 8, true>(a, num_sms, s)
+                            : launch_out_one<NT, 2, 8, false>(a, num_sms, s);
+  return bf16 ? launch_out_one<NT, 2, 4, true>(a, num_sms, s) : launch_out_one<NT, 2, 4, false>(a, num_sms, s);
+}
+
+}  // namespace alto
