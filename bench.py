@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--serve-pool", type=int, default=64)
     p.add_argument("--no-cpapr", action="store_true", help="skip the CP-APR measurement")
     p.add_argument("--cpapr-nnz", type=int, default=0, help="override the count tensor's nonzeros")
+    p.add_argument("--no-tune", action="store_true",
+                   help="library default plans instead of the autotuned ones")
     return p.parse_args()
 
 
@@ -158,10 +160,16 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def traffic_from_profiles(kernel_src_sha):
+PROFILE_OF_KERNEL = {"mttkrp_kernel": "mttkrp_zipf3d_10Mx2Mx50k_r32.md",
+                     "mttkrp_out_kernel": "mttkrp_out_zipf3d_10Mx2Mx50k_r32.md"}
+
+
+def traffic_from_profiles(kernel_src_sha, kernel="mttkrp_kernel"):
     """dram bytes per launch of the MTTKRP kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "mttkrp_zipf3d_10Mx2Mx50k_r32.md")
+    if kernel not in PROFILE_OF_KERNEL:
+        return None
+    path = os.path.join(ROOT, "profiles", PROFILE_OF_KERNEL[kernel])
     try:
         text = open(path).read()
     except OSError:
@@ -175,20 +183,24 @@ def traffic_from_profiles(kernel_src_sha):
 
 def kernel_src_sha():
     h = hashlib.sha256()
-    for f in ("mttkrp.cu", "mttkrp.cuh", "mttkrp_kernel.cuh", "alto_internal.cuh"):
+    for f in ("mttkrp.cu", "mttkrp.cuh", "mttkrp_kernel.cuh", "alto_internal.cuh", "outorder.cuh",
+              "out_n3.cu"):
         with open(os.path.join(ROOT, "paper_2403_06348_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes_per_mode(coords, dims, R, key_bytes, fbytes=4):
-    """M*(key+value bytes) + sum_{m!=n} D_m*R*fbytes + I_n*R*4, D_m = distinct rows."""
+def algorithmic_bytes_per_mode(coords, dims, R, key_bytes, fbytes=4, order_bytes=None):
+    """M*(key+value bytes) + sum_{m!=n} D_m*R*fbytes + I_n*R*4, D_m = distinct
+    rows; plus M*order_bytes[n] for a mode walked through its stored order."""
     M = coords.shape[1]
     D = [int(np.count_nonzero(np.bincount(coords[m], minlength=dims[m]))) for m in range(len(dims))]
     out = []
     for n in range(len(dims)):
         b = M * (key_bytes + 4) + sum(D[m] * R * fbytes for m in range(len(dims)) if m != n)
         b += dims[n] * R * 4
+        if order_bytes is not None:
+            b += M * order_bytes[n]
         out.append(b)
     return out, D
 
@@ -283,8 +295,22 @@ def run_ours(args):
     A0d = [torch.from_numpy(a).cuda() for a in A0]
     work = [torch.empty_like(a) for a in A0d]
 
+    # the per-mode plan, measured once on this workload before timing (the
+    # autotuner with the stored-order candidates, the default segment count)
+    plans = None
+    if not args.no_tune:
+        h = alto.alto_encode(coords_d, vals_d, dims)
+        out = torch.empty((max(dims), R), dtype=torch.float32, device="cuda")
+        rep = h.autotune(A0d, R, out=out, segments=False, output=True)
+        plans = rep["plans"]
+        del out
+        h.free()
+
     def step(profile_into=None):
         h = alto.alto_encode(coords_d, vals_d, dims)
+        if plans is not None:
+            for n, (variant, cpl, hot) in enumerate(plans):
+                h.set_mode_plan(n, variant, cpl, hot)
         if profile_into is not None:
             h.profile_enable(True)
         for w, a in zip(work, A0d):
@@ -332,14 +358,19 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the MTTKRP segment kernel)
     kw = prof.get("_kw", 1)
-    bytes_per_mode, distinct = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw)
+    used = prof.get("_plans") or []
+    outorder = [len(used) > n and used[n][0] == 3 for n in range(N)]
+    bytes_per_mode, distinct = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw,
+                                                          order_bytes=[4 if o else 0 for o in outorder])
+    kernel = ("mttkrp_out_kernel" if all(outorder) else
+              "mttkrp_kernel" if not any(outorder) else "mttkrp_out_kernel + mttkrp_kernel")
     n_mttkrp, ms_mttkrp = prof.get("mttkrp", (0, 0.0))
     avg_ms = ms_mttkrp / max(n_mttkrp, 1)
     avg_bytes = sum(bytes_per_mode) / N
     achieved = avg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
     peak, peak_src = measured_peaks()
     sha = kernel_src_sha()
-    traffic = traffic_from_profiles(sha)
+    traffic = traffic_from_profiles(sha, kernel)
     breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / args.steps}
                  for k, v in prof.items() if not k.startswith("_")}
 
@@ -351,7 +382,7 @@ def run_ours(args):
                                          "mode_plans": prof.get("_plans")}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "kernel": "mttkrp_kernel",
+                         "traffic": traffic, "kernel": kernel,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": avg_bytes,
                          "avg_launch_ms": avg_ms, "launches": n_mttkrp,
@@ -362,7 +393,7 @@ def run_ours(args):
             "final_fit": fits[-1] if fits else None}
 
     if not args.no_e2e:
-        line["e2e"] = run_e2e(args, alto, coords, vals, spec, A0, world, barrier)
+        line["e2e"] = run_e2e(args, alto, coords, vals, spec, A0, world, barrier, plans)
     if not args.no_serve:
         line["serving"] = run_serving(args, alto)
     if not args.no_cpapr and world == 1:
@@ -489,7 +520,7 @@ def run_cpapr(args, alto):
             "phi_nnz_r_per_s": M * R / (per / 1000.0) if evaluated else None}
 
 
-def run_e2e(args, alto, coords, vals, spec, A0, world, barrier):
+def run_e2e(args, alto, coords, vals, spec, A0, world, barrier, plans=None):
     """Same step through the C ABI with pinned HOST buffers: the library copies
     coords/values/factors in and the factors, lambda and fits out."""
     import torch
@@ -503,6 +534,9 @@ def run_e2e(args, alto, coords, vals, spec, A0, world, barrier):
 
     def step():
         h = alto.alto_encode(cn, vn, dims)
+        if plans is not None:
+            for n, (variant, cpl, hot) in enumerate(plans):
+                h.set_mode_plan(n, variant, cpl, hot)
         for w, a in zip(work, Ah):
             w.copy_(a)
         h.cpals(R, ITERS, wn)

@@ -202,7 +202,7 @@ alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan 
  *          not change a stored order.
  * Built on the device by one stable radix sort of (segment, coordinate) keys
  * (scratch of about 28 bytes per nonzero while it runs). Asynchronous.
- * Errors: INVALID_ARG (mode), UNSUPPORTED (nnz >= 2^32 - 512), OOM, CUDA.
+ * Errors: INVALID_ARG (mode), UNSUPPORTED (nnz > 2^32 - 4097), OOM, CUDA.
  * ------------------------------------------------------------------------- */
 alto_status alto_build_pos_out(alto_handle_t h, int mode, uint64_t nparts, void *stream);
 

@@ -423,9 +423,21 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
   const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
+    // recursive traversal (PULL) when the fiber reuse pays for buffered
+    // accumulation and the interval fits, else the output-oriented one
     const double reuse = (double)h->M / (double)h->dims[mode];
-    p.variant = (reuse > 4.0 && pull_fits) ? ALTO_VARIANT_PULL
-                                                                           : ALTO_VARIANT_ATOMIC;
+    if (reuse > 4.0 && pull_fits)
+      p.variant = ALTO_VARIANT_PULL;
+    else if (h->M <= kPosOutMaxNnz && !h->pos_out_failed[mode])
+      p.variant = ALTO_VARIANT_OUTPUT;
+    else
+      p.variant = ALTO_VARIANT_ATOMIC;
+    if (p.variant == ALTO_VARIANT_OUTPUT) {
+      p.cols_per_lane = (p.cols_per_lane >= 8 && R >= 8) ? 8 : 4;
+      p.hot_rows = 0;
+      *out = p;
+      return ALTO_OK;
+    }
   }
   if (p.variant == ALTO_VARIANT_PULL && !pull_fits)
     return fail(ALTO_ERR_UNSUPPORTED, "mode %d: interval of %u rows does not fit shared memory",
@@ -502,8 +514,15 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
     return ALTO_OK;
   }
+  if (p.variant == ALTO_VARIANT_OUTPUT && !h->pos_out[mode] &&
+      (st = set_pos_out(h, mode, 0, s)) != ALTO_OK) {
+    // AUTO falls back to ATOMIC when the order cannot be held; OUTPUT asked
+    // for by name reports the error
+    if (st != ALTO_ERR_OOM || h->plan[mode].variant != ALTO_VARIANT_AUTO) return st;
+    h->pos_out_failed[mode] = true;
+    if ((st = resolve_plan(h, mode, R, &p)) != ALTO_OK) return st;
+  }
   if (p.variant == ALTO_VARIANT_OUTPUT) {
-    if (!h->pos_out[mode] && (st = set_pos_out(h, mode, 0, s)) != ALTO_OK) return st;
     if (p.cols_per_lane == 8 && !bf16)
       for (int m = 0; m < h->N; ++m)
         if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;

@@ -123,6 +123,7 @@ struct alto_tensor {
   Buf partials;
   uint32_t *pos_out[alto::kMaxModes] = {};  // stored output-oriented order per mode
   uint64_t pos_out_L[alto::kMaxModes] = {}; // its segment count
+  bool pos_out_failed[alto::kMaxModes] = {};   // AUTO could not allocate it: ATOMIC
   // instrumentation
   bool prof_on = false;
   std::vector<ProfEvt> prof_pending;

@@ -76,6 +76,9 @@ cudaError_t launch_pull_reduce(const float *partials, const uint64_t *row_ptr, c
 cudaError_t launch_phi(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
                        cudaStream_t s);
 
+// Largest nnz with a stored output-oriented order (32-bit entries).
+constexpr uint64_t kPosOutMaxNnz = 0xFFFFFFFFull - 4096;
+
 // MTTKRP walking a.perm (the stored output-oriented order of a.mode).
 cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s);
 

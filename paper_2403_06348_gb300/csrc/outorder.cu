@@ -1,13 +1,15 @@
 // The stored output-oriented order pos_out of Alg. 4 and the dispatch of its
 // MTTKRP kernel by number of modes (kernels in outorder.cuh, out_n*.cu).
 //
-// pos_out of a mode is built as one stable LSD radix sort of the whole line:
-// the key of ordered position x is (segment of x, coordinate of the mode) and
-// the sorted values are the positions themselves. Segments are contiguous and
-// the sort is stable, so this is the per-segment stable sort by coordinate.
+// pos_out of a mode is the per-segment stable sort of positions by the mode's
+// coordinate. Segments that fit shared memory (the default partition always
+// does) are sorted one per CTA; otherwise the whole line goes through one
+// stable LSD radix sort whose key of ordered position x is (segment of x,
+// coordinate) and whose sorted values are the positions: segments are
+// contiguous and the sort is stable, so the result is the same.
 #include "encode.cuh"
 #include "handle.cuh"
-#include "outorder.cuh"
+#include "mttkrp.cuh"
 
 namespace alto {
 
@@ -30,6 +32,146 @@ __global__ void __launch_bounds__(256) pos_key_kernel(const __grid_constant__ De
     const uint64_t l = ((x + 1) * L - 1) / nnz;
     ck[x] = (l << bits) | i;
     pos[x] = (uint32_t)x;
+  }
+}
+
+// Segments of at most kSegCap nonzeros are sorted inside one CTA each: the
+// segment's (coordinate - segment minimum, local index) pairs sit in shared
+// memory and go through a stable LSD radix sort with 8-bit digits, as many
+// passes as the segment's coordinate range needs. Per pass, warp w ranks the
+// items of its contiguous share by digit (match_any; one writer per digit and
+// warp), a scan over the digit-major (digit, warp) count table gives every
+// warp's first slot per digit, and a second walk scatters the items.
+constexpr int kSegThreads = 512;
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr uint32_t kSegCap = 16384;
+constexpr size_t kSegSmem = (size_t)kSegCap * (4 + 2) * 2 + (size_t)256 * kSegWarps * 4;
+
+__device__ __forceinline__ unsigned seg_lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_constant__ DecodePlan dp,
+                                                              const uint64_t *__restrict__ keys,
+                                                              uint64_t nnz, uint64_t L, int mode,
+                                                              uint32_t *__restrict__ pos_out) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  uint32_t *ka = reinterpret_cast<uint32_t *>(sm);
+  uint32_t *kb = ka + kSegCap;
+  uint16_t *ia = reinterpret_cast<uint16_t *>(kb + kSegCap);
+  uint16_t *ib = ia + kSegCap;
+  uint32_t *wc = reinterpret_cast<uint32_t *>(ib + kSegCap);  // [256][kSegWarps]
+  __shared__ uint32_t red[2][kSegWarps];
+  __shared__ uint32_t part[kSegThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned full = 0xffffffffu;
+  for (uint64_t l = blockIdx.x; l < L; l += gridDim.x) {
+    const uint64_t s0 = l * nnz / L, s1 = (l + 1) * nnz / L;
+    const uint32_t S = (uint32_t)(s1 - s0);
+    uint32_t mn = 0xFFFFFFFFu, mx = 0;
+    for (uint32_t j = threadIdx.x; j < S; j += kSegThreads) {
+      uint32_t c[kMaxModes];
+      const uint64_t x = s0 + j;
+      decode_all<KW>(dp, keys[x * KW], KW == 2 ? keys[x * KW + 1] : 0ull, c);
+      uint32_t i = 0;
+#pragma unroll
+      for (int n = 0; n < kMaxModes; ++n)
+        if (n == mode) i = c[n];
+      ka[j] = i;
+      ia[j] = (uint16_t)j;
+      mn = min(mn, i);
+      mx = max(mx, i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(full, mn, o));
+      mx = max(mx, __shfl_xor_sync(full, mx, o));
+    }
+    if (lane == 0) {
+      red[0][warp] = mn;
+      red[1][warp] = mx;
+    }
+    __syncthreads();
+    mn = 0xFFFFFFFFu;
+    mx = 0;
+    for (int w = 0; w < kSegWarps; ++w) {
+      mn = min(mn, red[0][w]);
+      mx = max(mx, red[1][w]);
+    }
+    const uint32_t range = S ? mx - mn : 0u;
+    const int passes = (32 - __clz(range) + 7) / 8;  // __clz(0) = 32: no pass
+    // warp w's share [w * per, min(S, (w + 1) * per)), walked in rounds of 32
+    const uint32_t per = (S + kSegWarps - 1) / kSegWarps;
+    const uint32_t w0 = min(S, warp * per), w1 = min(S, w0 + per);
+    for (int p = 0; p < passes; ++p) {
+      const int shift = 8 * p;
+      for (int i = threadIdx.x; i < 256 * kSegWarps; i += kSegThreads) wc[i] = 0;
+      __syncthreads();
+      for (uint32_t base = w0; base < w1; base += 32) {
+        const uint32_t j = base + lane;
+        const uint32_t d = j < w1 ? ((ka[j] - mn) >> shift) & 0xFFu : 256u;
+        const unsigned peers = __match_any_sync(full, d);
+        if (d < 256u && (peers & seg_lanemask_lt()) == 0) wc[d * kSegWarps + warp] += __popc(peers);
+        __syncwarp();
+      }
+      __syncthreads();
+      {
+        // exclusive scan of the 256 x kSegWarps table, digit-major: thread t
+        // owns entries [8t, 8t + 8)
+        constexpr int kPer = 256 * kSegWarps / kSegThreads;
+        uint32_t v[kPer], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          v[k] = wc[threadIdx.x * kPer + k];
+          sum += v[k];
+        }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(full, inc, o);
+          if (lane >= o) inc += y;
+        }
+        if (lane == 31) part[warp] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += part[w];
+        uint32_t run = before + inc - sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          wc[threadIdx.x * kPer + k] = run;
+          run += v[k];
+        }
+      }
+      __syncthreads();
+      for (uint32_t base = w0; base < w1; base += 32) {
+        const uint32_t j = base + lane;
+        const bool ok = j < w1;
+        const uint32_t key = ok ? ka[j] : 0u;
+        const uint32_t d = ok ? ((key - mn) >> shift) & 0xFFu : 256u;
+        const unsigned peers = __match_any_sync(full, d);
+        uint32_t slot = 0;
+        if (ok) slot = wc[d * kSegWarps + warp] + __popc(peers & seg_lanemask_lt());
+        __syncwarp();
+        if (ok && (peers & seg_lanemask_lt()) == 0) wc[d * kSegWarps + warp] += __popc(peers);
+        if (ok) {
+          kb[slot] = key;
+          ib[slot] = ia[j];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      uint32_t *tk = ka;
+      ka = kb;
+      kb = tk;
+      uint16_t *ti = ia;
+      ia = ib;
+      ib = ti;
+    }
+    for (uint32_t j = threadIdx.x; j < S; j += kSegThreads) pos_out[s0 + j] = (uint32_t)(s0 + ia[j]);
+    __syncthreads();
   }
 }
 
@@ -69,6 +211,34 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
   uint32_t *res = static_cast<uint32_t *>(dalloc(h, std::max<uint64_t>(M, 1) * 4, s));
   if (!res) return fail(ALTO_ERR_OOM, "pos_out of %llu entries", (unsigned long long)M);
   if (M == 0) {
+    *out = res;
+    return ALTO_OK;
+  }
+  if ((M + L - 1) / L <= kSegCap) {
+    // every segment fits one CTA's shared memory
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e1 = cudaFuncSetAttribute(pos_seg_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kSegSmem);
+      cudaError_t e2 = cudaFuncSetAttribute(pos_seg_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kSegSmem);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        dfree(h, res, M * 4, s);
+        return fail(ALTO_ERR_CUDA, "pos_out: shared memory attribute");
+      }
+      attr_set = true;
+    }
+    const int grid = (int)std::min<uint64_t>(L, (uint64_t)h->num_sms);
+    if (h->kw == 1)
+      pos_seg_kernel<1><<<grid, kSegThreads, kSegSmem, s>>>(h->dp, h->keys, M, L, mode, res);
+    else
+      pos_seg_kernel<2><<<grid, kSegThreads, kSegSmem, s>>>(h->dp, h->keys, M, L, mode, res);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      dfree(h, res, M * 4, s);
+      return fail(ALTO_ERR_CUDA, "pos_out: %s", cudaGetErrorString(e));
+    }
     *out = res;
     return ALTO_OK;
   }

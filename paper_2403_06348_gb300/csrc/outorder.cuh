@@ -3,10 +3,10 @@
 //
 // The stored order pos_out lists, segment by segment, the ordered positions by
 // increasing output coordinate, so nonzeros of one output row sit next to each
-// other in it. Warps take chunks of 32 * kOutBatches consecutive entries of
-// pos_out; inside a chunk, each group of tpn = R / CPL lanes owns a contiguous
-// piece of tpn * kOutBatches entries and walks it in kOutBatches batches of
-// tpn nonzeros. The run of equal output row is carried in registers across
+// other in it. Warps take chunks of 32 * B consecutive entries of pos_out
+// (B = out_batches<CPL>()); inside a chunk, each group of tpn = R / CPL lanes
+// owns a contiguous piece of tpn * B entries and walks it in B batches of tpn
+// nonzeros. The run of equal output row is carried in registers across
 // the batches of the piece and leaves with one vector atomic per run (the
 // paper's boundary update), so the number of global updates is the number of
 // distinct rows per piece instead of the number of nonzeros. No shared memory.
@@ -16,16 +16,28 @@
 
 namespace alto {
 
-constexpr int kOutBatches = 16;
-// Largest nnz with a stored order: entries are 32-bit and a chunk may run up
-// to 32 * kOutBatches entries past the end.
-constexpr uint64_t kPosOutMaxNnz = 0xFFFFFFFFull - 32ull * kOutBatches;
+// Batches per piece at 4 columns per lane; 8-column lanes (half the lanes per
+// nonzero) take twice as many, so a piece holds 4 R entries either way.
+#ifndef ALTO_OUT_BATCHES
+#define ALTO_OUT_BATCHES 16
+#endif
+#ifndef ALTO_OUT_MIN_BLOCKS
+#define ALTO_OUT_MIN_BLOCKS 0  // 0: as the segment kernel (3 CTAs per SM, 2 for 8 columns)
+#endif
+template <int CPL>
+constexpr int out_batches() {
+  return ALTO_OUT_BATCHES * (CPL / 4);
+}
+// entries are 32-bit and a chunk may run up to one chunk past the end
+static_assert(32ull * ALTO_OUT_BATCHES * 2 <= 0xFFFFFFFFull - kPosOutMaxNnz, "chunk overruns 32 bits");
 
 template <int NT, int KW, int CPL, bool BF16>
-__global__ void __launch_bounds__(kMttkrpThreads, mttkrp_min_blocks<CPL>())
+__global__ void __launch_bounds__(kMttkrpThreads,
+                                  ALTO_OUT_MIN_BLOCKS ? ALTO_OUT_MIN_BLOCKS : mttkrp_min_blocks<CPL>())
     mttkrp_out_kernel(const __grid_constant__ MttkrpArgs a) {
   constexpr int NMAX = NT ? NT : kMaxModes;
   constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
+  constexpr int kOutBatches = out_batches<CPL>();
   const int N = NT ? NT : a.dp.nmodes;
   const int R = a.R;
   const int tpn = R / CPL;
@@ -129,7 +141,8 @@ __global__ void __launch_bounds__(kMttkrpThreads, mttkrp_min_blocks<CPL>())
 template <int NT, int KW, int CPL, bool BF16>
 static cudaError_t launch_out_one(const MttkrpArgs &a, int num_sms, cudaStream_t s) {
   auto kern = mttkrp_out_kernel<NT, KW, CPL, BF16>;
-  const uint64_t chunks = (a.nnz + 32ull * kOutBatches - 1) / (32ull * kOutBatches);
+  constexpr uint64_t chunk = 32ull * out_batches<CPL>();
+  const uint64_t chunks = (a.nnz + chunk - 1) / chunk;
   const uint64_t warps_per_cta = kMttkrpThreads / 32;
   uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, 0);
   const uint64_t need = (chunks + warps_per_cta - 1) / warps_per_cta;

@@ -35,7 +35,10 @@ def _zipf(dims, nnz, seed):
                                          ((300, 200, 24), 40_001, 7), ((500, 400, 30, 12), 30_011, 0),
                                          ((2_000_000, 100_000, 10_000, 1000, 50), 30_000, 0),
                                          ((2_000_000, 100_000, 10_000, 1000, 50), 30_000, 30_000),
-                                         ((50, 1, 40), 3_333, 5), ((7, 9, 5), 1, 0)])
+                                         ((50, 1, 40), 3_333, 5), ((7, 9, 5), 1, 0),
+                                         # segments of 16384 (one CTA each) and 16385 (one sort)
+                                         ((300, 200, 24), 32_768, 2), ((300, 200, 24), 32_769, 2),
+                                         ((1_000_000, 3, 1000), 250_000, 0)])
 def test_pos_out_equals_oracle(dims, nnz, L):
     coords, vals = _zipf(dims, nnz, 1 + nnz % 97)
     t = gu.encode(coords, vals, dims)
