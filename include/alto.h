@@ -535,12 +535,13 @@ alto_status alto_fill_uniform(float *dst, uint64_t n, uint64_t seed, void *strea
 typedef enum alto_prof_kind {
   ALTO_PROF_MTTKRP = 0,       /* the segment kernel of Alg. 3/4             */
   ALTO_PROF_PULL_REDUCE = 1,  /* the pull-based reduction of Alg. 4         */
-  ALTO_PROF_ZERO = 2,         /* zeroing of the output (ATOMIC variant)      */
+  ALTO_PROF_ZERO = 2,         /* zeroing of the output (ATOMIC, OUTPUT)      */
   ALTO_PROF_GRAM = 3,         /* A^T A of the initial factors                */
   ALTO_PROF_SOLVE = 4,        /* fp64 Hadamard / Cholesky / lambda / fit    */
   ALTO_PROF_RMUL = 5,         /* A^(n) = M V^-1 with its Gram (one pass) and
                                  the final column normalisation             */
-  ALTO_PROF_KINDS = 6
+  ALTO_PROF_POS_OUT = 6,      /* building a stored output-oriented order     */
+  ALTO_PROF_KINDS = 7
 } alto_prof_kind;
 
 typedef struct alto_profile {

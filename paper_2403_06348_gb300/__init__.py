@@ -56,7 +56,7 @@ class alto_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_size_t)]
 
 
-PROF_KINDS = ("mttkrp", "pull_reduce", "zero", "gram", "solve", "rmul")
+PROF_KINDS = ("mttkrp", "pull_reduce", "zero", "gram", "solve", "rmul", "pos_out")
 
 
 class alto_profile(ctypes.Structure):

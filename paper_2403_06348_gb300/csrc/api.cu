@@ -458,7 +458,11 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
 alto_status set_pos_out(alto_tensor *h, int n, uint64_t L, cudaStream_t s) {
   if (L == 0) L = h->L;
   uint32_t *po = nullptr;
-  alto_status st = build_pos_out(h, n, L, &po, s);
+  alto_status st;
+  {
+    ProfScope ps(h, ALTO_PROF_POS_OUT, s);
+    st = build_pos_out(h, n, L, &po, s);
+  }
   if (st != ALTO_OK) return st;
   dfree(h, h->pos_out[n], std::max<uint64_t>(h->M, 1) * 4, s);
   h->pos_out[n] = po;

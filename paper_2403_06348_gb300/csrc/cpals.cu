@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kUpdThreads, 2) update_kernel(const float *__r
   if (*done_at <= it) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   const uint64_t TR = 4096 / R;
-  update_body(const_cast<float *>(M), W, Bout, I, R, BtB, dot, blockIdx.x, gridDim.x, (I + TR - 1) / TR,
+  update_body<true>(const_cast<float *>(M), W, Bout, I, R, BtB, dot, blockIdx.x, gridDim.x, (I + TR - 1) / TR,
               false, smraw);
 }
 

@@ -237,6 +237,12 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
 // fp64. The CTA walks tiles t0, t0 + tstep, ... < t1 (TR rows each); with
 // clear_m it also zeroes the M rows it has read.
 
+// SYM: the Gram pass forms only the blocks of B^T B on and above the diagonal
+// (B4 (B4 + 1) / 2 of the B4^2 4 x 4 blocks) and mirrors them at the end;
+// worth it where one call covers many tiles (the single-tensor update). The
+// batch update, which calls this once per short tile range, keeps all blocks
+// and its cheap warp pre-reduction.
+template <bool SYM = false>
 __device__ __forceinline__ void update_body(float *M, const float *__restrict__ W,
                                             float *__restrict__ Bout, uint64_t I, int R,
                                             double *__restrict__ BtB, double *__restrict__ dot,
@@ -253,8 +259,19 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
   const int tid = threadIdx.x;
   const int B4 = R / 4;                      // column blocks
   const int cb = tid % B4, rb = tid / B4;    // phase 1: rows 4*rb .. 4*rb+3, cols 4*cb ..
-  const int BB = B4 * B4, RG = kUpdThreads / BB;
-  const int tb = tid % BB, rg = tid / BB, bi = tb / B4, bj = tb % B4;
+  const int BB = SYM ? B4 * (B4 + 1) / 2 : B4 * B4, RG = kUpdThreads / BB;
+  const int tb = tid % BB, rg = tid / BB;
+  int bi = tb / B4, bj = tb % B4;
+  if (SYM) {  // tb-th block of the upper triangle, row by row
+    int rem = tb;
+    bi = 0;
+    while (rem >= B4 - bi) {
+      rem -= B4 - bi;
+      ++bi;
+    }
+    bj = bi + rem;
+  }
+  const bool gram = rg < RG;  // SYM leaves kUpdThreads mod BB threads out
   for (int i = tid; i < R * R + R; i += kUpdThreads) red[i] = 0.0;
   for (int i = tid; i < R * R; i += kUpdThreads) w[i] = W[i];
   float g[4][4], dp[4];
@@ -333,7 +350,7 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
       if (r < nrows) *reinterpret_cast<float4 *>(Bout + (r0 + r) * (uint64_t)R + 4 * cb) = ov;
     }
     __syncthreads();
-    for (int r = rg; r < nrows; r += RG) {
+    for (int r = gram ? rg : nrows; r < nrows; r += RG) {
       const float4 xv = *reinterpret_cast<const float4 *>(bt + r * RP + 4 * bi);
       const float4 yv = *reinterpret_cast<const float4 *>(bt + r * RP + 4 * bj);
       const float xa[4] = {xv.x, xv.y, xv.z, xv.w}, ya[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -367,6 +384,13 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       double v = dg[x][y] + (double)g[x][y];
+      if (SYM) {
+        if (gram) {
+          atomicAdd(&red[(4 * bi + x) * R + 4 * bj + y], v);
+          if (bi != bj) atomicAdd(&red[(4 * bj + y) * R + 4 * bi + x], v);
+        }
+        continue;
+      }
       for (int o = 16; o >= BB; o >>= 1) v += __shfl_xor_sync(full, v, o);
       if (BB >= 32 || lane < BB) atomicAdd(&red[(4 * bi + x) * R + 4 * bj + y], v);
     }

@@ -13,22 +13,46 @@
 
 namespace alto {
 
+// The 32-bit runs of one mode (EXTRACT of Alg. 3 for that mode only).
+struct ModeRuns32 {
+  int nruns;
+  Run32 runs[kMaxRuns32];
+};
+
+template <int KW>
+__device__ __forceinline__ uint32_t decode_mode(const ModeRuns32 &mr, uint64_t lo, uint64_t hi) {
+  uint32_t v = 0;
+#pragma unroll
+  for (int r = 0; r < kMaxRuns32; ++r) {
+    if (r < mr.nruns) {
+      const Run32 &br = mr.runs[r];
+      uint32_t x = window32<KW>(lo, hi, br.start) & br.mask[0];
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if (j < br.steps) x = (x | (x >> br.sh[j])) & br.mask[j + 1];
+      v |= x << br.outshift;
+    }
+  }
+  return v;
+}
+
+static ModeRuns32 mode_runs(const alto_tensor *h, int mode) {
+  ModeRuns32 mr{};
+  mr.nruns = h->dp32.nruns[mode];
+  for (int r = 0; r < mr.nruns; ++r) mr.runs[r] = h->dp32.runs[mode][r];
+  return mr;
+}
+
 // key[x] = l(x) << bits | i_mode(x), pos[x] = x, where l(x) is the segment
 // [floor(l M / L), floor((l + 1) M / L)) holding x: l(x) = floor(((x + 1) L - 1) / M).
 template <int KW>
-__global__ void __launch_bounds__(256) pos_key_kernel(const __grid_constant__ DecodePlan dp,
+__global__ void __launch_bounds__(256) pos_key_kernel(const __grid_constant__ ModeRuns32 mr,
                                                       const uint64_t *__restrict__ keys, uint64_t nnz,
-                                                      uint64_t L, int mode, int bits,
-                                                      uint64_t *__restrict__ ck,
+                                                      uint64_t L, int bits, uint64_t *__restrict__ ck,
                                                       uint32_t *__restrict__ pos) {
   for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
        x += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t c[kMaxModes];
-    decode_all<KW>(dp, keys[x * KW], KW == 2 ? keys[x * KW + 1] : 0ull, c);
-    uint32_t i = 0;
-#pragma unroll
-    for (int n = 0; n < kMaxModes; ++n)
-      if (n == mode) i = c[n];
+    const uint32_t i = decode_mode<KW>(mr, keys[x * KW], KW == 2 ? keys[x * KW + 1] : 0ull);
     const uint64_t l = ((x + 1) * L - 1) / nnz;
     ck[x] = (l << bits) | i;
     pos[x] = (uint32_t)x;
@@ -42,7 +66,7 @@ __global__ void __launch_bounds__(256) pos_key_kernel(const __grid_constant__ De
 // items of its contiguous share by digit (match_any; one writer per digit and
 // warp), a scan over the digit-major (digit, warp) count table gives every
 // warp's first slot per digit, and a second walk scatters the items.
-constexpr int kSegThreads = 512;
+constexpr int kSegThreads = 1024;
 constexpr int kSegWarps = kSegThreads / 32;
 constexpr uint32_t kSegCap = 16384;
 constexpr size_t kSegSmem = (size_t)kSegCap * (4 + 2) * 2 + (size_t)256 * kSegWarps * 4;
@@ -54,9 +78,9 @@ __device__ __forceinline__ unsigned seg_lanemask_lt() {
 }
 
 template <int KW>
-__global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_constant__ DecodePlan dp,
+__global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_constant__ ModeRuns32 mr,
                                                               const uint64_t *__restrict__ keys,
-                                                              uint64_t nnz, uint64_t L, int mode,
+                                                              uint64_t nnz, uint64_t L,
                                                               uint32_t *__restrict__ pos_out) {
   extern __shared__ __align__(16) unsigned char sm[];
   uint32_t *ka = reinterpret_cast<uint32_t *>(sm);
@@ -72,14 +96,10 @@ __global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_const
     const uint64_t s0 = l * nnz / L, s1 = (l + 1) * nnz / L;
     const uint32_t S = (uint32_t)(s1 - s0);
     uint32_t mn = 0xFFFFFFFFu, mx = 0;
+#pragma unroll 8
     for (uint32_t j = threadIdx.x; j < S; j += kSegThreads) {
-      uint32_t c[kMaxModes];
       const uint64_t x = s0 + j;
-      decode_all<KW>(dp, keys[x * KW], KW == 2 ? keys[x * KW + 1] : 0ull, c);
-      uint32_t i = 0;
-#pragma unroll
-      for (int n = 0; n < kMaxModes; ++n)
-        if (n == mode) i = c[n];
+      const uint32_t i = decode_mode<KW>(mr, keys[x * KW], KW == 2 ? keys[x * KW + 1] : 0ull);
       ka[j] = i;
       ia[j] = (uint16_t)j;
       mn = min(mn, i);
@@ -170,6 +190,7 @@ __global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_const
       ia = ib;
       ib = ti;
     }
+#pragma unroll 8
     for (uint32_t j = threadIdx.x; j < S; j += kSegThreads) pos_out[s0 + j] = (uint32_t)(s0 + ia[j]);
     __syncthreads();
   }
@@ -229,10 +250,11 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
       attr_set = true;
     }
     const int grid = (int)std::min<uint64_t>(L, (uint64_t)h->num_sms);
+    const ModeRuns32 mr = mode_runs(h, mode);
     if (h->kw == 1)
-      pos_seg_kernel<1><<<grid, kSegThreads, kSegSmem, s>>>(h->dp, h->keys, M, L, mode, res);
+      pos_seg_kernel<1><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, M, L, res);
     else
-      pos_seg_kernel<2><<<grid, kSegThreads, kSegSmem, s>>>(h->dp, h->keys, M, L, mode, res);
+      pos_seg_kernel<2><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, M, L, res);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -255,10 +277,11 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
     return fail(ALTO_ERR_OOM, "pos_out sort scratch for %llu entries", (unsigned long long)M);
   }
   const int grid = (int)std::min<uint64_t>((M + 255) / 256, (uint64_t)h->num_sms * 8);
+  const ModeRuns32 mr = mode_runs(h, mode);
   if (h->kw == 1)
-    pos_key_kernel<1><<<grid, 256, 0, s>>>(h->dp, h->keys, M, L, mode, bits, kbuf[0], pos);
+    pos_key_kernel<1><<<grid, 256, 0, s>>>(mr, h->keys, M, L, bits, kbuf[0], pos);
   else
-    pos_key_kernel<2><<<grid, 256, 0, s>>>(h->dp, h->keys, M, L, mode, bits, kbuf[0], pos);
+    pos_key_kernel<2><<<grid, 256, 0, s>>>(mr, h->keys, M, L, bits, kbuf[0], pos);
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   int fbuf = 0;

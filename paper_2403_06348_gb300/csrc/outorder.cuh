@@ -21,9 +21,14 @@ namespace alto {
 #ifndef ALTO_OUT_BATCHES
 #define ALTO_OUT_BATCHES 16
 #endif
+#ifndef ALTO_OUT_UNROLL
+#define ALTO_OUT_UNROLL 2  // rounds (nonzeros of a group) unrolled together
+#endif
 #ifndef ALTO_OUT_MIN_BLOCKS
 #define ALTO_OUT_MIN_BLOCKS 0  // 0: as the segment kernel (3 CTAs per SM, 2 for 8 columns)
 #endif
+constexpr int kOutUnroll = ALTO_OUT_UNROLL;
+
 template <int CPL>
 constexpr int out_batches() {
   return ALTO_OUT_BATCHES * (CPL / 4);
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(kMttkrpThreads,
       for (int k = 0; k < NIN; ++k) in[k] = (NMAX > 1 && k + 1 < NMAX) ? (k < ro ? c[k] : c[k + 1]) : 0u;
       const unsigned live = __ballot_sync(full, valid);
       if (!live) break;
-#pragma unroll(CPL <= 8 ? 2 : 1)
+#pragma unroll(CPL <= 8 ? kOutUnroll : 1)
       for (int q = 0; q < tpn; ++q) {
         const int j = grp * tpn + q;
         const float vj = __shfl_sync(full, v, j);

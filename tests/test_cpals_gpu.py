@@ -23,7 +23,7 @@ def _oracle_cpals(coords, vals, dims, init, iters, tol=0.0):
     return ar.cp_als(coords, vals, dims, init, iters, tol=tol)
 
 
-@pytest.mark.parametrize("R", [8, 16])
+@pytest.mark.parametrize("R", [4, 8, 16, 32, 64])
 def test_fit_trajectory_matches_oracle(R):
     spec = synth.scaled(synth.CONFIGS[0], 20_000, dims=(200, 160, 120))
     coords, vals = synth.generate(spec)
