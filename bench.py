@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--cpapr-nnz", type=int, default=0, help="override the count tensor's nonzeros")
     p.add_argument("--no-tune", action="store_true",
                    help="library default plans instead of the autotuned ones")
+    p.add_argument("--plans", default="",
+                   help="per-mode plans 'variant:cols_per_lane,...' instead of tuning (profiling)")
     return p.parse_args()
 
 
@@ -298,7 +300,10 @@ def run_ours(args):
     # the per-mode plan, measured once on this workload before timing (the
     # autotuner with the stored-order candidates, the default segment count)
     plans = None
-    if not args.no_tune:
+    if args.plans:
+        plans = [(int(v), int(c), 0 if int(v) == 3 else -1)
+                 for v, c in (x.split(":") for x in args.plans.split(","))]
+    elif not args.no_tune:
         h = alto.alto_encode(coords_d, vals_d, dims)
         out = torch.empty((max(dims), R), dtype=torch.float32, device="cuda")
         rep = h.autotune(A0d, R, out=out, segments=False, output=True)

@@ -67,10 +67,15 @@ typedef enum alto_dtype { ALTO_F32 = 0, ALTO_BF16 = 1 } alto_dtype;
  *          are consecutive in it, each group of threads walks a contiguous
  *          piece of it, sums each run of equal row in registers across the
  *          whole piece and adds the run to the output with one vector atomic.
- *          Costs 4 bytes per nonzero for the mode's stored order.
- *  AUTO:   PULL when the fiber reuse nnz/dims[mode] exceeds 4 (the paper's
- *          cost of buffered accumulation) and the largest interval fits in
- *          shared memory, else ATOMIC (never OUTPUT, which needs memory). */
+ *          The stored order holds, per nonzero, its ordered position (4
+ *          bytes), its line position (8 * key_words bytes) and its value (4
+ *          bytes): pos_out and val_out of Alg. 4, read as one stream.
+ *  AUTO:   OUTPUT (measured faster on GB300 than PULL and ATOMIC for modes
+ *          of any reuse); if the order cannot be allocated (or nnz is too
+ *          large for it), the paper's rule: PULL when the fiber reuse
+ *          nnz/dims[mode] exceeds 4 (the paper's cost of buffered
+ *          accumulation) and the largest interval fits in shared memory,
+ *          else ATOMIC. */
 typedef enum alto_variant {
   ALTO_VARIANT_AUTO = 0,
   ALTO_VARIANT_ATOMIC = 1,
@@ -192,16 +197,19 @@ alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan 
  * every line segment l of nparts, [floor(l*nnz/nparts),
  * floor((l+1)*nnz/nparts)) as in Section IV-A, the segment's ordered
  * positions by increasing coordinate of the mode; equal coordinates keep line
- * order. Kept in the handle as nnz uint32 positions per mode (4 bytes per
- * nonzero per mode: the paper keeps one tensor copy, the order costs this
- * much on top), replacing an earlier order of that mode, until
- * alto_free_pos_out or alto_free. The ALTO_VARIANT_OUTPUT plan walks it.
+ * order. Kept in the handle per mode, replacing an earlier order of that
+ * mode, until alto_free_pos_out or alto_free: the nnz uint32 ordered
+ * positions and, in that order, the line positions and values (Alg. 4's
+ * pos_out and val_out), 4 + 8 * key_words + 4 bytes per nonzero per mode on
+ * top of the one ALTO copy. The ALTO_VARIANT_OUTPUT plan streams it.
  *
  *  nparts  segments of the order; 0 = the handle's current segment count,
  *          values above nnz count as nnz. Later alto_set_partitions calls do
  *          not change a stored order.
- * Built on the device by one stable radix sort of (segment, coordinate) keys
- * (scratch of about 28 bytes per nonzero while it runs). Asynchronous.
+ * Built on the device: one CTA sorts each segment in shared memory when every
+ * segment holds at most 16384 nonzeros (the default partition does), else
+ * one stable radix sort of (segment, coordinate) keys runs over the whole
+ * line (scratch of about 28 bytes per nonzero). Asynchronous.
  * Errors: INVALID_ARG (mode), UNSUPPORTED (nnz > 2^32 - 4097), OOM, CUDA.
  * ------------------------------------------------------------------------- */
 alto_status alto_build_pos_out(alto_handle_t h, int mode, uint64_t nparts, void *stream);

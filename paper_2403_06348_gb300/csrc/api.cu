@@ -423,13 +423,16 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   const size_t pull_smem = mttkrp_smem_bytes(true, R, 0, 0, h->max_interval[mode]);
   const bool pull_fits = pull_smem <= mttkrp_smem_limit() && h->M > 0;
   if (p.variant == ALTO_VARIANT_AUTO) {
-    // recursive traversal (PULL) when the fiber reuse pays for buffered
-    // accumulation and the interval fits, else the output-oriented one
+    // The output-oriented traversal through the stored order whenever the
+    // order can be held: on this GPU it beats the recursive one (PULL) even
+    // for modes of high fiber reuse. Otherwise the paper's rule: PULL when
+    // the reuse pays for buffered accumulation and the interval fits, else
+    // ATOMIC.
     const double reuse = (double)h->M / (double)h->dims[mode];
-    if (reuse > 4.0 && pull_fits)
-      p.variant = ALTO_VARIANT_PULL;
-    else if (h->M <= kPosOutMaxNnz && !h->pos_out_failed[mode])
+    if (h->M <= kPosOutMaxNnz && !h->pos_out_failed[mode])
       p.variant = ALTO_VARIANT_OUTPUT;
+    else if (reuse > 4.0 && pull_fits)
+      p.variant = ALTO_VARIANT_PULL;
     else
       p.variant = ALTO_VARIANT_ATOMIC;
     if (p.variant == ALTO_VARIANT_OUTPUT) {
@@ -453,28 +456,49 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   return ALTO_OK;
 }
 
+void free_pos_out(alto_tensor *h, int n, cudaStream_t s) {
+  const uint64_t M1 = std::max<uint64_t>(h->M, 1);
+  dfree(h, h->pos_out[n], M1 * 4, s);
+  dfree(h, h->keys_out[n], M1 * h->kw * 8, s);
+  dfree(h, h->vals_out[n], M1 * 4, s);
+  h->pos_out[n] = nullptr;
+  h->keys_out[n] = nullptr;
+  h->vals_out[n] = nullptr;
+  h->pos_out_L[n] = 0;
+}
+
 // Builds (or rebuilds) the stored order of mode n with L segments (0 = the
 // current count) and keeps it in the handle.
 alto_status set_pos_out(alto_tensor *h, int n, uint64_t L, cudaStream_t s) {
   if (L == 0) L = h->L;
+  const uint64_t M1 = std::max<uint64_t>(h->M, 1);
   uint32_t *po = nullptr;
+  uint64_t *ko = nullptr;
+  float *vo = nullptr;
   alto_status st;
   {
     ProfScope ps(h, ALTO_PROF_POS_OUT, s);
-    st = build_pos_out(h, n, L, &po, s);
+    ko = static_cast<uint64_t *>(dalloc(h, M1 * h->kw * 8, s));
+    vo = static_cast<float *>(dalloc(h, M1 * 4, s));
+    if (!ko || !vo)
+      st = fail(ALTO_ERR_OOM, "output-ordered copy of %llu nonzeros", (unsigned long long)h->M);
+    else
+      st = build_pos_out(h, n, L, &po, ko, vo, s);
   }
-  if (st != ALTO_OK) return st;
-  dfree(h, h->pos_out[n], std::max<uint64_t>(h->M, 1) * 4, s);
+  if (st != ALTO_OK) {
+    dfree(h, po, M1 * 4, s);
+    dfree(h, ko, M1 * h->kw * 8, s);
+    dfree(h, vo, M1 * 4, s);
+    return st;
+  }
+  free_pos_out(h, n, s);
   h->pos_out[n] = po;
+  h->keys_out[n] = ko;
+  h->vals_out[n] = vo;
   h->pos_out_L[n] = h->M ? std::min<uint64_t>(std::max<uint64_t>(L, 1), h->M) : 1;
   return ALTO_OK;
 }
 
-void free_pos_out(alto_tensor *h, int n, cudaStream_t s) {
-  dfree(h, h->pos_out[n], std::max<uint64_t>(h->M, 1) * 4, s);
-  h->pos_out[n] = nullptr;
-  h->pos_out_L[n] = 0;
-}
 
 alto_status check_handle(alto_tensor *h) {
   if (!h) return fail(ALTO_ERR_INVALID_ARG, "null handle");
@@ -531,6 +555,8 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
       for (int m = 0; m < h->N; ++m)
         if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
     a.perm = h->pos_out[mode];
+    a.keys = h->keys_out[mode];
+    a.vals = h->vals_out[mode];
     {
       ProfScope ps(h, ALTO_PROF_ZERO, s);
       CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
@@ -591,19 +617,22 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Phi^(n) of Alg. 5 into phi (which the ATOMIC variant needs zeroed; the
-// caller's inner_begin kernel does that) with the same per-mode conflict
-// resolution as the MTTKRP: hot rows staged (ATOMIC) or segment Temp and the
-// pull reduction (PULL). 4 fp32 columns per lane.
+// Phi^(n) of Alg. 5 into phi (which the ATOMIC and OUTPUT variants need
+// zeroed; the caller's inner_begin kernel does that) with the same per-mode
+// conflict resolution as the MTTKRP: hot rows staged (ATOMIC), segment Temp
+// and the pull reduction (PULL), or the stored output-oriented order
+// (OUTPUT). 4 fp32 columns per lane.
 alto_status phi_impl(alto_tensor *h, int mode, const float *const *A, const float *B,
                      const float *pimat, float eps, int R, float *phi, const int *skip,
                      cudaStream_t s) {
   alto_mode_plan p;
   alto_status st = resolve_plan(h, mode, R, &p);
   if (st != ALTO_OK) return st;
-  if (p.variant == ALTO_VARIANT_OUTPUT) {  // Phi has no stored-order kernel: ATOMIC
-    p.variant = ALTO_VARIANT_ATOMIC;
-    p.hot_rows = hot_slots_that_fit(R, (int)h->nhot[mode]);
+  if (p.variant == ALTO_VARIANT_OUTPUT && !h->pos_out[mode] && h->M > 0 &&
+      (st = set_pos_out(h, mode, 0, s)) != ALTO_OK) {
+    if (st != ALTO_ERR_OOM || h->plan[mode].variant != ALTO_VARIANT_AUTO) return st;
+    h->pos_out_failed[mode] = true;  // AUTO: ATOMIC from now on
+    if ((st = resolve_plan(h, mode, R, &p)) != ALTO_OK) return st;
   }
   MttkrpArgs a{};
   a.bp = h->bp;
@@ -637,7 +666,12 @@ alto_status phi_impl(alto_tensor *h, int mode, const float *const *A, const floa
   }
   if (h->M == 0) return ALTO_OK;
   const bool pre = pimat != nullptr;
-  if (p.variant == ALTO_VARIANT_PULL) {
+  if (p.variant == ALTO_VARIANT_OUTPUT) {
+    a.perm = h->pos_out[mode];
+    a.keys = h->keys_out[mode];
+    a.vals = h->vals_out[mode];
+    CUDA_TRY(launch_phi_out(a, pre, h->num_sms, s));
+  } else if (p.variant == ALTO_VARIANT_PULL) {
     if ((st = ensure_pull(h, mode, s)) != ALTO_OK) return st;
     const PullPlan &pp = h->pull[mode];
     const size_t need = pp.total_rows * (size_t)R * sizeof(float);

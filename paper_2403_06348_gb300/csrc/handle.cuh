@@ -67,9 +67,18 @@ alto_status ensure_group_hot(alto_tensor *h, int n, int nslots, cudaStream_t s,
 
 // pos_out of Alg. 4 for one mode: inside every segment l of L, the ordered
 // positions by increasing coordinate of `mode`, ties in line order, as nnz
-// uint32 positions in *out (needs nnz < 2^32). Scratch and result come from
-// the handle's allocator; the result is the caller's (4 * nnz bytes).
-alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, cudaStream_t s);
+// uint32 positions in *out (needs nnz < 2^32), and in that order the line
+// positions (keys_out, nnz * kw words) and values (vals_out), both allocated
+// by the caller. Scratch and *out come from the handle's allocator; *out is
+// the caller's (4 * nnz bytes).
+alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, uint64_t *keys_out,
+                          float *vals_out, cudaStream_t s);
+
+// keys_out[p] = keys[perm[p]], vals_out[p] = vals[perm[p]] (the line
+// positions and values in the stored order).
+cudaError_t launch_gather_out(const uint32_t *perm, const uint64_t *keys, const float *vals,
+                              uint64_t nnz, int kw, uint64_t *keys_out, float *vals_out, int num_sms,
+                              cudaStream_t s);
 
 }  // namespace alto
 
@@ -122,6 +131,8 @@ struct alto_tensor {
   PullPlan pull[alto::kMaxModes];
   Buf partials;
   uint32_t *pos_out[alto::kMaxModes] = {};  // stored output-oriented order per mode
+  uint64_t *keys_out[alto::kMaxModes] = {}; // line positions in that order [nnz][kw]
+  float *vals_out[alto::kMaxModes] = {};    // values in that order
   uint64_t pos_out_L[alto::kMaxModes] = {}; // its segment count
   bool pos_out_failed[alto::kMaxModes] = {};   // AUTO could not allocate it: ATOMIC
   // instrumentation

@@ -85,6 +85,12 @@ cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_s
 template <int NT>
 cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s);
 
+// Phi (Alg. 5) walking a.perm: a.bmat set, a.pimat set for PRE.
+cudaError_t launch_phi_out(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s);
+
+template <int NT>
+cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s);
+
 template <int NT>
 cudaError_t launch_phi_nt(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
                           cudaStream_t s);

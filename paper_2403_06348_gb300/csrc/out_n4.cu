@@ -1,6 +1,7 @@
-// Output-oriented MTTKRP kernels specialised for 4 modes.
+// Output-oriented MTTKRP and Phi kernels specialised for 4 modes.
 #include "outorder.cuh"
 
 namespace alto {
 template cudaError_t launch_mttkrp_out_nt<4>(const MttkrpArgs &, int, bool, int, cudaStream_t);
+template cudaError_t launch_phi_out_nt<4>(const MttkrpArgs &, bool, int, cudaStream_t);
 }  // namespace alto

@@ -80,8 +80,11 @@ __device__ __forceinline__ unsigned seg_lanemask_lt() {
 template <int KW>
 __global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_constant__ ModeRuns32 mr,
                                                               const uint64_t *__restrict__ keys,
+                                                              const float *__restrict__ vals,
                                                               uint64_t nnz, uint64_t L,
-                                                              uint32_t *__restrict__ pos_out) {
+                                                              uint32_t *__restrict__ pos_out,
+                                                              uint64_t *__restrict__ keys_out,
+                                                              float *__restrict__ vals_out) {
   extern __shared__ __align__(16) unsigned char sm[];
   uint32_t *ka = reinterpret_cast<uint32_t *>(sm);
   uint32_t *kb = ka + kSegCap;
@@ -190,8 +193,16 @@ __global__ void __launch_bounds__(kSegThreads) pos_seg_kernel(const __grid_const
       ia = ib;
       ib = ti;
     }
-#pragma unroll 8
-    for (uint32_t j = threadIdx.x; j < S; j += kSegThreads) pos_out[s0 + j] = (uint32_t)(s0 + ia[j]);
+    // the order, and the segment's line positions and values in it (the
+    // segment was just read: its keys come from L2)
+#pragma unroll 4
+    for (uint32_t j = threadIdx.x; j < S; j += kSegThreads) {
+      const uint64_t x = s0 + ia[j];
+      pos_out[s0 + j] = (uint32_t)x;
+#pragma unroll
+      for (int w = 0; w < KW; ++w) keys_out[(s0 + j) * KW + w] = keys[x * KW + w];
+      vals_out[s0 + j] = vals[x];
+    }
     __syncthreads();
   }
 }
@@ -205,7 +216,8 @@ static int bit_width_u64(uint64_t v) {
   return b;
 }
 
-alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, cudaStream_t s) {
+alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, uint64_t *keys_out,
+                          float *vals_out, cudaStream_t s) {
   *out = nullptr;
   const uint64_t M = h->M;
   if (M > kPosOutMaxNnz)
@@ -252,9 +264,11 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
     const int grid = (int)std::min<uint64_t>(L, (uint64_t)h->num_sms);
     const ModeRuns32 mr = mode_runs(h, mode);
     if (h->kw == 1)
-      pos_seg_kernel<1><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, M, L, res);
+      pos_seg_kernel<1><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, h->vals, M, L, res, keys_out,
+                                                            vals_out);
     else
-      pos_seg_kernel<2><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, M, L, res);
+      pos_seg_kernel<2><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, h->vals, M, L, res, keys_out,
+                                                            vals_out);
     note_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -302,8 +316,41 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
     res = reinterpret_cast<uint32_t *>(vbuf[1]);
     release(1);
   }
+  e = launch_gather_out(res, h->keys, h->vals, M, h->kw, keys_out, vals_out, h->num_sms, s);
+  if (e != cudaSuccess) {
+    dfree(h, res, M * 4, s);
+    return fail(ALTO_ERR_CUDA, "pos_out copy: %s", cudaGetErrorString(e));
+  }
   *out = res;
   return ALTO_OK;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) gather_out_kernel(const uint32_t *__restrict__ perm,
+                                                         const uint64_t *__restrict__ keys,
+                                                         const float *__restrict__ vals, uint64_t nnz,
+                                                         uint64_t *__restrict__ keys_out,
+                                                         float *__restrict__ vals_out) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t x = perm[p];
+#pragma unroll
+    for (int w = 0; w < KW; ++w) keys_out[p * KW + w] = keys[x * KW + w];
+    vals_out[p] = vals[x];
+  }
+}
+
+cudaError_t launch_gather_out(const uint32_t *perm, const uint64_t *keys, const float *vals,
+                              uint64_t nnz, int kw, uint64_t *keys_out, float *vals_out, int num_sms,
+                              cudaStream_t s) {
+  if (nnz == 0) return cudaSuccess;
+  const int grid = (int)std::min<uint64_t>((nnz + 255) / 256, (uint64_t)num_sms * 16);
+  if (kw == 1)
+    gather_out_kernel<1><<<grid, 256, 0, s>>>(perm, keys, vals, nnz, keys_out, vals_out);
+  else
+    gather_out_kernel<2><<<grid, 256, 0, s>>>(perm, keys, vals, nnz, keys_out, vals_out);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s) {
@@ -313,6 +360,16 @@ cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_s
     case 4: return launch_mttkrp_out_nt<4>(a, cpl, bf16, num_sms, s);
     case 5: return launch_mttkrp_out_nt<5>(a, cpl, bf16, num_sms, s);
     default: return launch_mttkrp_out_nt<0>(a, cpl, bf16, num_sms, s);
+  }
+}
+
+cudaError_t launch_phi_out(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s) {
+  if (a.nnz == 0) return cudaSuccess;
+  switch (a.dp.nmodes) {
+    case 3: return launch_phi_out_nt<3>(a, pre, num_sms, s);
+    case 4: return launch_phi_out_nt<4>(a, pre, num_sms, s);
+    case 5: return launch_phi_out_nt<5>(a, pre, num_sms, s);
+    default: return launch_phi_out_nt<0>(a, pre, num_sms, s);
   }
 }
 

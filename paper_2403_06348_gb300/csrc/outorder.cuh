@@ -1,9 +1,9 @@
 // MTTKRP with output-oriented traversal (Alg. 4, the pos_out branch),
 // included by the per-mode-count instantiation units out_n*.cu.
 //
-// The stored order pos_out lists, segment by segment, the ordered positions by
-// increasing output coordinate, so nonzeros of one output row sit next to each
-// other in it. Warps take chunks of 32 * B consecutive entries of pos_out
+// The stored order (pos_out / val_out of Alg. 4: the line positions and values
+// of every segment's nonzeros by increasing output coordinate) puts nonzeros
+// of one output row next to each other. Warps take chunks of 32 * B consecutive entries of pos_out
 // (B = out_batches<CPL>()); inside a chunk, each group of tpn = R / CPL lanes
 // owns a contiguous piece of tpn * B entries and walks it in B batches of tpn
 // nonzeros. The run of equal output row is carried in registers across
@@ -36,10 +36,16 @@ constexpr int out_batches() {
 // entries are 32-bit and a chunk may run up to one chunk past the end
 static_assert(32ull * ALTO_OUT_BATCHES * 2 <= 0xFFFFFFFFull - kPosOutMaxNnz, "chunk overruns 32 bits");
 
-template <int NT, int KW, int CPL, bool BF16>
+// APR != kAprOff computes the CP-APR model update Phi (Alg. 5) with the same
+// traversal: the group's Khatri-Rao row (gathered, or row x of the
+// precomputed Pi, x the nonzero's line position) dotted with B(i_n, :) over
+// the group's lanes, and the run receives v / max(dot, eps) * krp.
+template <int NT, int KW, int CPL, bool BF16, int APR = kAprOff>
 __global__ void __launch_bounds__(kMttkrpThreads,
                                   ALTO_OUT_MIN_BLOCKS ? ALTO_OUT_MIN_BLOCKS : mttkrp_min_blocks<CPL>())
     mttkrp_out_kernel(const __grid_constant__ MttkrpArgs a) {
+  static_assert(APR == kAprOff || (CPL == 4 && !BF16), "Phi uses 4 fp32 columns per lane");
+  if (APR != kAprOff && a.skip && *a.skip) return;  // CP-APR inner loop already converged
   constexpr int NMAX = NT ? NT : kMaxModes;
   constexpr int NIN = NMAX > 1 ? NMAX - 1 : 1;
   constexpr int kOutBatches = out_batches<CPL>();
@@ -65,31 +71,27 @@ __global__ void __launch_bounds__(kMttkrpThreads,
   const uint32_t piece = (uint32_t)tpn * kOutBatches;
 
   for (uint32_t ch = warp_id; ch < nchunks; ch += nwarps) {
-    // entry of pos_out this lane loads in batch b: p0 + b * tpn
+    // entry of the stored order this lane loads in batch b: p0 + b * tpn
+    // (a.keys / a.vals hold the line positions and values in that order)
     const uint32_t p0 = ch * chunk + (uint32_t)grp * piece + (uint32_t)sub;
-    uint32_t idx_next = 0, idx_after = 0;
     uint64_t nlo = 0, nhi = 0;
     float nv = 0.f;
-    auto load_idx = [&](int b) -> uint32_t {
-      const uint32_t p = p0 + (uint32_t)(b * tpn);
-      return (b < kOutBatches && p < nnz) ? __ldcs(a.perm + p) : 0u;
-    };
-    auto load_nz = [&](int b, uint32_t x) {
+    uint32_t nx = 0;  // PRE: the nonzero's line position (its row of Pi)
+    auto load_nz = [&](int b) {
       const uint32_t p = p0 + (uint32_t)(b * tpn);
       if (b < kOutBatches && p < nnz) {
         if (KW == 1) {
-          nlo = __ldg(reinterpret_cast<const unsigned long long *>(a.keys) + x);
+          nlo = __ldcs(reinterpret_cast<const unsigned long long *>(a.keys) + p);
         } else {
-          const ulonglong2 kk = __ldg(reinterpret_cast<const ulonglong2 *>(a.keys) + x);
+          const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2 *>(a.keys) + p);
           nlo = kk.x;
           nhi = kk.y;
         }
-        nv = __ldg(a.vals + x);
+        nv = __ldcs(a.vals + p);
+        if (APR == kAprPre) nx = __ldcs(a.perm + p);
       }
     };
-    idx_next = load_idx(0);
-    idx_after = load_idx(1);
-    load_nz(0, idx_next);
+    load_nz(0);
 
     float run[CPL];
 #pragma unroll
@@ -99,10 +101,9 @@ __global__ void __launch_bounds__(kMttkrpThreads,
       const bool valid = p0 + (uint32_t)(b * tpn) < nnz;
       const uint64_t lo = nlo, hi = nhi;
       const float v = nv;
-      // the next batch's nonzero and the entry after it are loaded while this one runs
-      const uint32_t x_next = idx_after;
-      idx_after = load_idx(b + 2);
-      load_nz(b + 1, x_next);
+      const uint32_t xb = nx;
+      // the next batch's nonzero is loaded while this one runs
+      load_nz(b + 1);
       uint32_t c[NMAX];
       if constexpr (NT > 0)
         decode_blocks<KW, NMAX, 0>(a.bp, lo, hi, c);
@@ -124,10 +125,45 @@ __global__ void __launch_bounds__(kMttkrpThreads,
         const uint32_t rj = __shfl_sync(full, row, j);
         uint32_t ij[NIN];
 #pragma unroll
-        for (int k = 0; k < NIN; ++k) ij[k] = (k + 1 < N) ? __shfl_sync(full, in[k], j) : 0u;
-        if (!((live >> j) & 1u)) continue;
+        for (int k = 0; k < NIN; ++k)
+          ij[k] = (APR != kAprPre && k + 1 < N) ? __shfl_sync(full, in[k], j) : 0u;
+        const bool live_j = (live >> j) & 1u;
         float p[CPL];
-        gather_product<NMAX, CPL, BF16>(fb, ij, rowb, tpn, N, vj, p);
+        if constexpr (APR != kAprOff) {
+          float kr[4] = {1.f, 1.f, 1.f, 1.f};
+          if (APR == kAprPre) {
+            const uint32_t xj = __shfl_sync(full, xb, j);
+            if (live_j) {
+              const float4 qv = __ldg(reinterpret_cast<const float4 *>(a.pimat) +
+                                      (uint64_t)xj * (uint64_t)(R / 4) + sub);
+              kr[0] = qv.x;
+              kr[1] = qv.y;
+              kr[2] = qv.z;
+              kr[3] = qv.w;
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) {
+              if (k + 1 < N) {
+                const float4 qv = __ldg(reinterpret_cast<const float4 *>(fb[k] + (uint64_t)ij[k] * rowb));
+                kr[0] *= qv.x;
+                kr[1] *= qv.y;
+                kr[2] *= qv.z;
+                kr[3] *= qv.w;
+              }
+            }
+          }
+          const float4 bv = __ldg(reinterpret_cast<const float4 *>(a.bmat) + (uint64_t)rj * (R / 4) + sub);
+          float dot = kr[0] * bv.x + kr[1] * bv.y + kr[2] * bv.z + kr[3] * bv.w;
+          for (int o = 1; o < tpn; o <<= 1) dot += __shfl_xor_sync(full, dot, o);
+          if (!live_j) continue;
+          const float scale = vj / fmaxf(dot, a.eps);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) p[cc] = scale * kr[cc];
+        } else {
+          if (!live_j) continue;
+          gather_product<NMAX, CPL, BF16>(fb, ij, rowb, tpn, N, vj, p);
+        }
         if (rj == run_row) {
 #pragma unroll
           for (int cc = 0; cc < CPL; ++cc) run[cc] += p[cc];
@@ -143,9 +179,9 @@ __global__ void __launch_bounds__(kMttkrpThreads,
   }
 }
 
-template <int NT, int KW, int CPL, bool BF16>
+template <int NT, int KW, int CPL, bool BF16, int APR = kAprOff>
 static cudaError_t launch_out_one(const MttkrpArgs &a, int num_sms, cudaStream_t s) {
-  auto kern = mttkrp_out_kernel<NT, KW, CPL, BF16>;
+  auto kern = mttkrp_out_kernel<NT, KW, CPL, BF16, APR>;
   constexpr uint64_t chunk = 32ull * out_batches<CPL>();
   const uint64_t chunks = (a.nnz + chunk - 1) / chunk;
   const uint64_t warps_per_cta = kMttkrpThreads / 32;
@@ -168,6 +204,15 @@ cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, int nu
   if (cpl == 8) return bf16 ? launch_out_one<NT, 2, 8, true>(a, num_sms, s)
                             : launch_out_one<NT, 2, 8, false>(a, num_sms, s);
   return bf16 ? launch_out_one<NT, 2, 4, true>(a, num_sms, s) : launch_out_one<NT, 2, 4, false>(a, num_sms, s);
+}
+
+template <int NT>
+cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s) {
+  if (a.dp.kw == 1)
+    return pre ? launch_out_one<NT, 1, 4, false, kAprPre>(a, num_sms, s)
+               : launch_out_one<NT, 1, 4, false, kAprOtf>(a, num_sms, s);
+  return pre ? launch_out_one<NT, 2, 4, false, kAprPre>(a, num_sms, s)
+             : launch_out_one<NT, 2, 4, false, kAprOtf>(a, num_sms, s);
 }
 
 }  // namespace alto

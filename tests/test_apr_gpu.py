@@ -36,7 +36,7 @@ def _pos(dims, R, seed):
     return [(0.1 + rng.random((d, R))).astype(np.float32) for d in dims]
 
 
-@pytest.mark.parametrize("variant", [1, 2])          # ATOMIC, PULL
+@pytest.mark.parametrize("variant", [1, 2, 3])       # ATOMIC, PULL, OUTPUT
 @pytest.mark.parametrize("pre", [False, True])
 @pytest.mark.parametrize("R", [4, 16, 32])
 def test_phi_matches_oracle(variant, pre, R):
@@ -56,13 +56,16 @@ def test_phi_matches_oracle(variant, pre, R):
         assert err <= 1e-5, f"mode {n} R {R} pre {pre}: {err:.3g}"
 
 
-def test_phi_four_and_five_modes_wide_keys():
-    for dims in [(500, 400, 30, 12), (2_000_000, 100_000, 10_000, 1000, 50)]:
+@pytest.mark.parametrize("variant", [1, 3])          # ATOMIC, OUTPUT
+def test_phi_four_and_five_modes_wide_keys(variant):
+    for dims in [(500, 400, 30, 12), (2_000_000, 100_000, 10_000, 1000, 50),
+                 (40, 30, 20, 10, 8, 6)]:
         coords, vals = _count_tensor(dims, 30_000, 6)
         t = gu.encode(coords, vals, dims)
         A = _pos(dims, 16, 7)
         Ad = gu.gpu_factors(A)
         for n in range(len(dims)):
+            t.set_mode_plan(n, variant, 4)
             B = _pos([dims[n]], 16, 8)[0]
             for pre in (False, True):
                 got = t.phi(n, Ad, gu.to_dev(B), 16, pre=pre).cpu().numpy()
@@ -118,6 +121,26 @@ def test_cpapr_exact_model_is_a_fixed_point():
     Ad = gu.gpu_factors([a.astype(np.float32) for a in init])
     got = t.cpapr(R, Ad, k_max=5)
     assert got["converged"] and got["outer_done"] == 1 and got["inner_steps_total"] == 0
+
+
+def test_cpapr_output_traversal_follows_the_oracle():
+    """Every mode on the stored output-oriented order (OUTPUT), PRE and OTF."""
+    import paper_2403_06348_gb300 as alto
+    dims, R = (200, 150, 24), 8
+    coords, vals = _count_tensor(dims, 20_000, 9)
+    init = _pos(dims, R, 10)
+    ref = apr.cp_apr_mu(coords, vals, dims, init, k_max=6)
+    for variant in (alto.APR_OTF, alto.APR_PRE):
+        t = gu.encode(coords, vals, dims)
+        for n in range(3):
+            t.set_mode_plan(n, alto.VARIANT_OUTPUT, 4)
+        got = t.cpapr(R, gu.gpu_factors(init), k_max=6, variant=variant)
+        k = min(got["outer_done"], ref.outer_done)
+        same = 0
+        while same < k and got["inner"][same] == ref.inner[same]:
+            same += 1
+        assert same >= 2, (got["inner"], ref.inner)
+        np.testing.assert_allclose(got["objective"][:same], ref.objective[:same], rtol=1e-5)
 
 
 def test_cpapr_pre_equals_otf_and_host_factors():

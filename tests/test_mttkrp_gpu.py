@@ -96,7 +96,9 @@ def test_count_tensor_small_modes_pull():
     spec = synth.scaled(synth.CONFIGS[2], 2_000_000)
     coords, vals = synth.generate(spec)
     t, _ = _run_modes(coords, vals, spec.dims, 16, seed=6)
-    assert t.get_mode_plan(3, 16)[0] == 2   # 24 rows, reuse 83k: pull
+    assert t.get_mode_plan(3, 16)[0] == 3   # AUTO: the stored output-oriented order
+    # the recursive traversal on the 200- and 24-row modes (reuse 10k, 83k)
+    _run_modes(coords, vals, spec.dims, 16, variant=2, seed=6, modes=[2, 3])
     _run_modes(coords, vals, spec.dims, 16, variant=2, seed=6, modes=[2, 3])
     _run_modes(coords, vals, spec.dims, 16, variant=2, seed=6, modes=[2, 3], cpl=16)
     _run_modes(coords, vals, spec.dims, 16, variant=1, seed=6, modes=[2, 3])

@@ -116,7 +116,8 @@ def test_output_built_on_first_use_and_freed():
     before = t.query().device_bytes
     t.set_mode_plan(1, OUTPUT, 4)
     _check(t, coords, vals, dims, A, Ad, 8, [1], 1e-5)
-    assert t.query().device_bytes == before + 4 * 5_000   # mode 1's order only
+    # mode 1's order: positions (4 B), line positions (8 B) and values (4 B) per nonzero
+    assert t.query().device_bytes == before + 16 * 5_000
     got, L = t.pos_out(1)
     np.testing.assert_array_equal(got.astype(np.int64), ar.pos_out(ar.encode(coords, vals, dims), L, 1))
     # the stored order does not follow later re-partitioning
@@ -127,7 +128,7 @@ def test_output_built_on_first_use_and_freed():
     _check(t, coords, vals, dims, A, Ad, 8, [1], 1e-5)
     held = t.query().device_bytes      # the re-partition changed the interval table's size
     t.free_pos_out(-1)
-    assert t.query().device_bytes == held - 4 * 5_000
+    assert t.query().device_bytes == held - 16 * 5_000
     _check(t, coords, vals, dims, A, Ad, 8, [1], 1e-5)   # rebuilt on use
 
 
