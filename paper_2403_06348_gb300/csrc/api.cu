@@ -405,6 +405,29 @@ int hot_slots_that_fit(int R, int want) {
   return k;
 }
 
+// Hot rows the OUTPUT kernels stage: the most frequent sampled rows, as many
+// as fit the shared memory of three CTAs per SM, at most kOutHotSlots. Runs of
+// other rows meet at most their number of pieces of additions in fp32.
+constexpr int kOutHotSlots = 256;
+
+int out_hot_slots(const alto_tensor *h, int mode, int R) {
+  return hot_slots_within(R, std::min<int>((int)h->nhot[mode], kOutHotSlots), stage_budget());
+}
+
+// The staged hot rows of mode n for an OUTPUT launch; *smem its shared memory.
+alto_status out_staging(alto_tensor *h, int n, int R, MttkrpArgs &a, size_t *smem, cudaStream_t s) {
+  const int nslots = out_hot_slots(h, n, R);
+  alto_status st = ensure_hot_table(h, n, nslots, s);
+  if (st != ALTO_OK) return st;
+  const HotTable &ht = h->hot_tab[n];
+  a.htab = ht.htab;
+  a.slot_rows = h->hot_rows[n];
+  a.hbits = ht.hbits;
+  a.nslots = ht.nslots;
+  *smem = mttkrp_smem_bytes(false, R, ht.nslots, ht.hbits, 0);
+  return ALTO_OK;
+}
+
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   alto_mode_plan p = h->plan[mode];
   if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16 &&
@@ -416,7 +439,7 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   if (p.cols_per_lane > 16 && p.cols_per_lane != R) p.cols_per_lane = 16;
   if (p.variant == ALTO_VARIANT_OUTPUT) {
     p.cols_per_lane = (p.cols_per_lane >= 8 && R >= 8) ? 8 : 4;
-    p.hot_rows = 0;
+    p.hot_rows = out_hot_slots(h, mode, R);
     *out = p;
     return ALTO_OK;
   }
@@ -437,7 +460,7 @@ alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
       p.variant = ALTO_VARIANT_ATOMIC;
     if (p.variant == ALTO_VARIANT_OUTPUT) {
       p.cols_per_lane = (p.cols_per_lane >= 8 && R >= 8) ? 8 : 4;
-      p.hot_rows = 0;
+      p.hot_rows = out_hot_slots(h, mode, R);
       *out = p;
       return ALTO_OK;
     }
@@ -557,12 +580,14 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     a.perm = h->pos_out[mode];
     a.keys = h->keys_out[mode];
     a.vals = h->vals_out[mode];
+    size_t smem = 0;
+    if ((st = out_staging(h, mode, R, a, &smem, s)) != ALTO_OK) return st;
     {
       ProfScope ps(h, ALTO_PROF_ZERO, s);
       CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
     }
     ProfScope ps(h, ALTO_PROF_MTTKRP, s);
-    CUDA_TRY(launch_mttkrp_out(a, p.cols_per_lane, bf16, h->num_sms, s));
+    CUDA_TRY(launch_mttkrp_out(a, p.cols_per_lane, bf16, smem, h->num_sms, s));
     return ALTO_OK;
   }
   if (p.variant == ALTO_VARIANT_PULL) {
@@ -670,7 +695,9 @@ alto_status phi_impl(alto_tensor *h, int mode, const float *const *A, const floa
     a.perm = h->pos_out[mode];
     a.keys = h->keys_out[mode];
     a.vals = h->vals_out[mode];
-    CUDA_TRY(launch_phi_out(a, pre, h->num_sms, s));
+    size_t smem = 0;
+    if ((st = out_staging(h, mode, R, a, &smem, s)) != ALTO_OK) return st;
+    CUDA_TRY(launch_phi_out(a, pre, smem, h->num_sms, s));
   } else if (p.variant == ALTO_VARIANT_PULL) {
     if ((st = ensure_pull(h, mode, s)) != ALTO_OK) return st;
     const PullPlan &pp = h->pull[mode];

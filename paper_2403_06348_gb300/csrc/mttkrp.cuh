@@ -79,17 +79,21 @@ cudaError_t launch_phi(const MttkrpArgs &a, bool pull, bool pre, size_t smem, in
 // Largest nnz with a stored output-oriented order (32-bit entries).
 constexpr uint64_t kPosOutMaxNnz = 0xFFFFFFFFull - 4096;
 
-// MTTKRP walking a.perm (the stored output-oriented order of a.mode).
-cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s);
+// MTTKRP over the stored output-oriented order of a.mode (a.keys / a.vals in
+// that order, a.perm its ordered positions); a.htab .. a.nslots the staged hot
+// rows (nslots 0: none), smem = mttkrp_smem_bytes(false, R, nslots, hbits, 0).
+cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, size_t smem, int num_sms,
+                              cudaStream_t s);
 
 template <int NT>
-cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s);
+cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, size_t smem, int num_sms,
+                                 cudaStream_t s);
 
-// Phi (Alg. 5) walking a.perm: a.bmat set, a.pimat set for PRE.
-cudaError_t launch_phi_out(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s);
+// Phi (Alg. 5) over the stored order: a.bmat set, a.pimat set for PRE.
+cudaError_t launch_phi_out(const MttkrpArgs &a, bool pre, size_t smem, int num_sms, cudaStream_t s);
 
 template <int NT>
-cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s);
+cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, size_t smem, int num_sms, cudaStream_t s);
 
 template <int NT>
 cudaError_t launch_phi_nt(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,

@@ -353,23 +353,24 @@ cudaError_t launch_gather_out(const uint32_t *perm, const uint64_t *keys, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s) {
+cudaError_t launch_mttkrp_out(const MttkrpArgs &a, int cpl, bool bf16, size_t smem, int num_sms,
+                              cudaStream_t s) {
   if (a.nnz == 0) return cudaSuccess;
   switch (a.dp.nmodes) {
-    case 3: return launch_mttkrp_out_nt<3>(a, cpl, bf16, num_sms, s);
-    case 4: return launch_mttkrp_out_nt<4>(a, cpl, bf16, num_sms, s);
-    case 5: return launch_mttkrp_out_nt<5>(a, cpl, bf16, num_sms, s);
-    default: return launch_mttkrp_out_nt<0>(a, cpl, bf16, num_sms, s);
+    case 3: return launch_mttkrp_out_nt<3>(a, cpl, bf16, smem, num_sms, s);
+    case 4: return launch_mttkrp_out_nt<4>(a, cpl, bf16, smem, num_sms, s);
+    case 5: return launch_mttkrp_out_nt<5>(a, cpl, bf16, smem, num_sms, s);
+    default: return launch_mttkrp_out_nt<0>(a, cpl, bf16, smem, num_sms, s);
   }
 }
 
-cudaError_t launch_phi_out(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s) {
+cudaError_t launch_phi_out(const MttkrpArgs &a, bool pre, size_t smem, int num_sms, cudaStream_t s) {
   if (a.nnz == 0) return cudaSuccess;
   switch (a.dp.nmodes) {
-    case 3: return launch_phi_out_nt<3>(a, pre, num_sms, s);
-    case 4: return launch_phi_out_nt<4>(a, pre, num_sms, s);
-    case 5: return launch_phi_out_nt<5>(a, pre, num_sms, s);
-    default: return launch_phi_out_nt<0>(a, pre, num_sms, s);
+    case 3: return launch_phi_out_nt<3>(a, pre, smem, num_sms, s);
+    case 4: return launch_phi_out_nt<4>(a, pre, smem, num_sms, s);
+    case 5: return launch_phi_out_nt<5>(a, pre, smem, num_sms, s);
+    default: return launch_phi_out_nt<0>(a, pre, smem, num_sms, s);
   }
 }
 

@@ -36,6 +36,20 @@ constexpr int out_batches() {
 // entries are 32-bit and a chunk may run up to one chunk past the end
 static_assert(32ull * ALTO_OUT_BATCHES * 2 <= 0xFFFFFFFFull - kPosOutMaxNnz, "chunk overruns 32 bits");
 
+// A run of at least kStageMinRun nonzeros may belong to a hot row whose runs
+// span many pieces: it is looked up in the staged table (shared memory) and
+// added there if found. Shorter runs go straight to the output; the lookup
+// stays off the path of the many short runs of cold rows.
+constexpr int kStageMinRun = 8;
+
+template <int CPL>
+__device__ __forceinline__ void flush_out_run(const float (&run)[CPL], uint32_t row, int n, bool staged,
+                                              const uint64_t *htab, const MttkrpArgs &a, float *temp,
+                                              int sub, int tpn, int grp) {
+  const int slot = (staged && n >= kStageMinRun) ? hot_lookup(htab, a.hbits, row) : -1;
+  flush_run<CPL>(run, row, slot, temp, a.out, a.R, sub, tpn, grp);
+}
+
 // APR != kAprOff computes the CP-APR model update Phi (Alg. 5) with the same
 // traversal: the group's Khatri-Rao row (gathered, or row x of the
 // precomputed Pi, x the nonzero's line position) dotted with B(i_n, :) over
@@ -61,6 +75,20 @@ __global__ void __launch_bounds__(kMttkrpThreads,
   const char *fb[NIN];
 #pragma unroll
   for (int k = 0; k < NIN; ++k) fb[k] = static_cast<const char *>(a.fin[k]) + inb;
+
+  // The sampled hot rows of the mode are staged in shared memory for the
+  // whole launch: a Zipf head spans thousands of pieces, and adding each
+  // piece's run to global memory would chain that many fp32 additions.
+  extern __shared__ __align__(16) unsigned char sm[];
+  float *temp = reinterpret_cast<float *>(sm);
+  uint64_t *htab = reinterpret_cast<uint64_t *>(temp + (size_t)a.nslots * R);
+  const bool staged = a.nslots > 0;
+  if (staged) {
+    const int hsize = 1 << a.hbits;
+    for (int i = threadIdx.x; i < hsize; i += blockDim.x) htab[i] = a.htab[i];
+    for (int i = threadIdx.x; i < a.nslots * R; i += blockDim.x) temp[i] = 0.f;
+    __syncthreads();
+  }
 
   // 32-bit entry arithmetic: pos_out exists only for nnz <= kPosOutMaxNnz
   const uint32_t nnz = (uint32_t)a.nnz;
@@ -97,6 +125,7 @@ __global__ void __launch_bounds__(kMttkrpThreads,
 #pragma unroll
     for (int c = 0; c < CPL; ++c) run[c] = 0.f;
     uint32_t run_row = kEmptyRow;
+    int run_n = 0;  // nonzeros in the run
     for (int b = 0; b < kOutBatches; ++b) {
       const bool valid = p0 + (uint32_t)(b * tpn) < nnz;
       const uint64_t lo = nlo, hi = nhi;
@@ -167,52 +196,77 @@ __global__ void __launch_bounds__(kMttkrpThreads,
         if (rj == run_row) {
 #pragma unroll
           for (int cc = 0; cc < CPL; ++cc) run[cc] += p[cc];
+          ++run_n;
         } else {
-          if (run_row != kEmptyRow) flush_run<CPL, false>(run, run_row, -1, nullptr, a.out, R, sub, tpn, grp);
+          if (run_row != kEmptyRow) flush_out_run<CPL>(run, run_row, run_n, staged, htab, a, temp, sub, tpn, grp);
 #pragma unroll
           for (int cc = 0; cc < CPL; ++cc) run[cc] = p[cc];
           run_row = rj;
+          run_n = 1;
         }
       }
     }
-    if (run_row != kEmptyRow) flush_run<CPL, false>(run, run_row, -1, nullptr, a.out, R, sub, tpn, grp);
+    if (run_row != kEmptyRow) flush_out_run<CPL>(run, run_row, run_n, staged, htab, a, temp, sub, tpn, grp);
+  }
+  if (staged) {  // the staged hot rows leave once per CTA
+    __syncthreads();
+    const float4 *t4 = reinterpret_cast<const float4 *>(temp);
+    const int n4 = a.nslots * R / 4;
+    const int per_row = R / 4;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+      const float4 t = t4[i];
+      if (t.x != 0.f || t.y != 0.f || t.z != 0.f || t.w != 0.f) {
+        const int sl = i / per_row, c4 = ((i - sl * per_row) * 4) ^ slot_swizzle(sl, R);
+        red_v4(a.out + (uint64_t)a.slot_rows[sl] * (uint64_t)R + c4, t.x, t.y, t.z, t.w);
+      }
+    }
   }
 }
 
 template <int NT, int KW, int CPL, bool BF16, int APR = kAprOff>
-static cudaError_t launch_out_one(const MttkrpArgs &a, int num_sms, cudaStream_t s) {
+static cudaError_t launch_out_one(const MttkrpArgs &a, size_t smem, int num_sms, cudaStream_t s) {
   auto kern = mttkrp_out_kernel<NT, KW, CPL, BF16, APR>;
+  static int configured = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mttkrp_smem_limit());
+    if (e != cudaSuccess) return e;
+    configured = 1;
+  }
   constexpr uint64_t chunk = 32ull * out_batches<CPL>();
   const uint64_t chunks = (a.nnz + chunk - 1) / chunk;
   const uint64_t warps_per_cta = kMttkrpThreads / 32;
-  uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, 0);
+  uint64_t grid = (uint64_t)num_sms * resident_ctas(kern, smem);
   const uint64_t need = (chunks + warps_per_cta - 1) / warps_per_cta;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kMttkrpThreads, 0, s>>>(a);
+  kern<<<(unsigned)grid, kMttkrpThreads, smem, s>>>(a);
   note_launches(1);
   return cudaGetLastError();
 }
 
 template <int NT>
-cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, int num_sms, cudaStream_t s) {
+cudaError_t launch_mttkrp_out_nt(const MttkrpArgs &a, int cpl, bool bf16, size_t smem, int num_sms,
+                                 cudaStream_t s) {
   if (a.dp.kw == 1) {
-    if (cpl == 8) return bf16 ? launch_out_one<NT, 1, 8, true>(a, num_sms, s)
-                              : launch_out_one<NT, 1, 8, false>(a, num_sms, s);
-    return bf16 ? launch_out_one<NT, 1, 4, true>(a, num_sms, s) : launch_out_one<NT, 1, 4, false>(a, num_sms, s);
+    if (cpl == 8) return bf16 ? launch_out_one<NT, 1, 8, true>(a, smem, num_sms, s)
+                              : launch_out_one<NT, 1, 8, false>(a, smem, num_sms, s);
+    return bf16 ? launch_out_one<NT, 1, 4, true>(a, smem, num_sms, s)
+                : launch_out_one<NT, 1, 4, false>(a, smem, num_sms, s);
   }
-  if (cpl == 8) return bf16 ? launch_out_one<NT, 2, 8, true>(a, num_sms, s)
-                            : launch_out_one<NT, 2, 8, false>(a, num_sms, s);
-  return bf16 ? launch_out_one<NT, 2, 4, true>(a, num_sms, s) : launch_out_one<NT, 2, 4, false>(a, num_sms, s);
+  if (cpl == 8) return bf16 ? launch_out_one<NT, 2, 8, true>(a, smem, num_sms, s)
+                            : launch_out_one<NT, 2, 8, false>(a, smem, num_sms, s);
+  return bf16 ? launch_out_one<NT, 2, 4, true>(a, smem, num_sms, s)
+              : launch_out_one<NT, 2, 4, false>(a, smem, num_sms, s);
 }
 
 template <int NT>
-cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, int num_sms, cudaStream_t s) {
+cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, size_t smem, int num_sms, cudaStream_t s) {
   if (a.dp.kw == 1)
-    return pre ? launch_out_one<NT, 1, 4, false, kAprPre>(a, num_sms, s)
-               : launch_out_one<NT, 1, 4, false, kAprOtf>(a, num_sms, s);
-  return pre ? launch_out_one<NT, 2, 4, false, kAprPre>(a, num_sms, s)
-             : launch_out_one<NT, 2, 4, false, kAprOtf>(a, num_sms, s);
+    return pre ? launch_out_one<NT, 1, 4, false, kAprPre>(a, smem, num_sms, s)
+               : launch_out_one<NT, 1, 4, false, kAprOtf>(a, smem, num_sms, s);
+  return pre ? launch_out_one<NT, 2, 4, false, kAprPre>(a, smem, num_sms, s)
+             : launch_out_one<NT, 2, 4, false, kAprOtf>(a, smem, num_sms, s);
 }
 
 }  // namespace alto

@@ -114,10 +114,13 @@ def test_output_built_on_first_use_and_freed():
     A = gu.rand_factors(dims, 8, 9)
     Ad = gu.gpu_factors(A)
     before = t.query().device_bytes
-    t.set_mode_plan(1, OUTPUT, 4)
-    _check(t, coords, vals, dims, A, Ad, 8, [1], 1e-5)
+    t.build_pos_out(1)
     # mode 1's order: positions (4 B), line positions (8 B) and values (4 B) per nonzero
     assert t.query().device_bytes == before + 16 * 5_000
+    t.free_pos_out(1)
+    assert t.query().device_bytes == before
+    t.set_mode_plan(1, OUTPUT, 4)
+    _check(t, coords, vals, dims, A, Ad, 8, [1], 1e-5)   # built on first use
     got, L = t.pos_out(1)
     np.testing.assert_array_equal(got.astype(np.int64), ar.pos_out(ar.encode(coords, vals, dims), L, 1))
     # the stored order does not follow later re-partitioning
