@@ -204,12 +204,13 @@ alto_status alto_get_mode_plan(alto_handle_t h, int mode, int R, alto_mode_plan 
  * top of the one ALTO copy. The ALTO_VARIANT_OUTPUT plan streams it.
  *
  *  nparts  segments of the order; 0 = the handle's current segment count,
- *          values above nnz count as nnz. Later alto_set_partitions calls do
- *          not change a stored order.
+ *          raised where needed so that no segment holds more than 8192
+ *          nonzeros; values above nnz count as nnz. Later
+ *          alto_set_partitions calls do not change a stored order.
  * Built on the device: one CTA sorts each segment in shared memory when every
- * segment holds at most 16384 nonzeros (the default partition does), else
- * one stable radix sort of (segment, coordinate) keys runs over the whole
- * line (scratch of about 28 bytes per nonzero). Asynchronous.
+ * segment holds at most 8192 nonzeros (the default count does), else one
+ * stable radix sort of (segment, coordinate) keys runs over the whole line
+ * (scratch of about 28 bytes per nonzero). Asynchronous.
  * Errors: INVALID_ARG (mode), UNSUPPORTED (nnz > 2^32 - 4097), OOM, CUDA.
  * ------------------------------------------------------------------------- */
 alto_status alto_build_pos_out(alto_handle_t h, int mode, uint64_t nparts, void *stream);

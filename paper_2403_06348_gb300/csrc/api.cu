@@ -493,7 +493,9 @@ void free_pos_out(alto_tensor *h, int n, cudaStream_t s) {
 // Builds (or rebuilds) the stored order of mode n with L segments (0 = the
 // current count) and keeps it in the handle.
 alto_status set_pos_out(alto_tensor *h, int n, uint64_t L, cudaStream_t s) {
-  if (L == 0) L = h->L;
+  // default: the handle's segments, cut finer where they exceed what one CTA
+  // sorts in shared memory
+  if (L == 0) L = std::max<uint64_t>(h->L, (h->M + kPosOutSegCap - 1) / kPosOutSegCap);
   const uint64_t M1 = std::max<uint64_t>(h->M, 1);
   uint32_t *po = nullptr;
   uint64_t *ko = nullptr;

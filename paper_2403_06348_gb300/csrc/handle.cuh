@@ -65,6 +65,10 @@ alto_status repartition(alto_tensor *h, uint64_t L, cudaStream_t s);
 alto_status ensure_group_hot(alto_tensor *h, int n, int nslots, cudaStream_t s,
                              const HotTable **out);
 
+// Largest segment of the stored order that one CTA sorts in shared memory;
+// by default the order's segments are at most this long.
+constexpr uint64_t kPosOutSegCap = 8192;
+
 // pos_out of Alg. 4 for one mode: inside every segment l of L, the ordered
 // positions by increasing coordinate of `mode`, ties in line order, as nnz
 // uint32 positions in *out (needs nnz < 2^32), and in that order the line

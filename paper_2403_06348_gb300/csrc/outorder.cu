@@ -2,8 +2,8 @@
 // MTTKRP kernel by number of modes (kernels in outorder.cuh, out_n*.cu).
 //
 // pos_out of a mode is the per-segment stable sort of positions by the mode's
-// coordinate. Segments that fit shared memory (the default partition always
-// does) are sorted one per CTA; otherwise the whole line goes through one
+// coordinate. Segments of at most kPosOutSegCap nonzeros (the default count
+// of the stored order guarantees it) are sorted one per CTA in shared memory; otherwise the whole line goes through one
 // stable LSD radix sort whose key of ordered position x is (segment of x,
 // coordinate) and whose sorted values are the positions: segments are
 // contiguous and the sort is stable, so the result is the same.
@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(256) pos_key_kernel(const __grid_constant__ Mo
 // items of its contiguous share by digit (match_any; one writer per digit and
 // warp), a scan over the digit-major (digit, warp) count table gives every
 // warp's first slot per digit, and a second walk scatters the items.
-constexpr int kSegThreads = 1024;
+constexpr int kSegThreads = 512;
 constexpr int kSegWarps = kSegThreads / 32;
-constexpr uint32_t kSegCap = 16384;
+constexpr uint32_t kSegCap = kPosOutSegCap;  // two sorting CTAs fit one SM
 constexpr size_t kSegSmem = (size_t)kSegCap * (4 + 2) * 2 + (size_t)256 * kSegWarps * 4;
 
 __device__ __forceinline__ unsigned seg_lanemask_lt() {
@@ -261,7 +261,7 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
       }
       attr_set = true;
     }
-    const int grid = (int)std::min<uint64_t>(L, (uint64_t)h->num_sms);
+    const int grid = (int)std::min<uint64_t>(L, (uint64_t)h->num_sms * 2);
     const ModeRuns32 mr = mode_runs(h, mode);
     if (h->kw == 1)
       pos_seg_kernel<1><<<grid, kSegThreads, kSegSmem, s>>>(mr, h->keys, h->vals, M, L, res, keys_out,

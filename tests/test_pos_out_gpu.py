@@ -36,14 +36,14 @@ def _zipf(dims, nnz, seed):
                                          ((2_000_000, 100_000, 10_000, 1000, 50), 30_000, 0),
                                          ((2_000_000, 100_000, 10_000, 1000, 50), 30_000, 30_000),
                                          ((50, 1, 40), 3_333, 5), ((7, 9, 5), 1, 0),
-                                         # segments of 16384 (one CTA each) and 16385 (one sort)
-                                         ((300, 200, 24), 32_768, 2), ((300, 200, 24), 32_769, 2),
+                                         # segments of 8192 (one CTA each) and 8193 (one sort)
+                                         ((300, 200, 24), 16_384, 2), ((300, 200, 24), 16_385, 2),
                                          ((1_000_000, 3, 1000), 250_000, 0)])
 def test_pos_out_equals_oracle(dims, nnz, L):
     coords, vals = _zipf(dims, nnz, 1 + nnz % 97)
     t = gu.encode(coords, vals, dims)
     ref_t = ar.encode(coords, vals, dims)
-    Lused = L if L else int(t.query().nparts)
+    Lused = L if L else max(int(t.query().nparts), -(-nnz // 8192))
     t.build_pos_out(-1, L)
     for n in range(len(dims)):
         got, Lgot = t.pos_out(n)
