@@ -33,7 +33,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MTTKRP nnz*R/s & HBM GB/s vs peak; served CP-ALS p50/p99 vs one-at-a-time"
 UNIT = "nnz*R/s"
-CONFIG_INDEX = 1
 ITERS = 10
 FALLBACK_HBM_GBS = 6800.0
 
@@ -82,7 +81,7 @@ def dist_env():
 
 def workload(args):
     import synth
-    spec = synth.CONFIGS[CONFIG_INDEX]
+    spec = synth.ZIPF3D  # 10M x 2M x 50k, 1e8 nonzeros, Zipf 1.1, R = 32
     if args.nnz:
         spec = synth.scaled(spec, args.nnz)
     return spec
@@ -493,7 +492,7 @@ def run_cpapr(args, alto):
     events inside the library."""
     import torch
     import synth
-    spec = synth.CONFIGS[2]
+    spec = synth.COUNT4D
     if args.cpapr_nnz:
         spec = synth.scaled(spec, args.cpapr_nnz)
     coords, vals = synth.cached(spec)

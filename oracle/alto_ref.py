@@ -4,7 +4,7 @@ Everything here is fp64 (or exact integers) and follows the paper's text in
 the order it states the steps. Only tests/, __graft_entry__.smoke() and
 bench.py's CPU legs may use it.
 
-Readings of the paper that this file fixes (each also listed in the design doc):
+Readings of the paper that this file fixes:
 
 * Coordinates are 0-based, as in the worked example of Fig. 3(a).
 * "log2 I_n" bits per mode (Eq. 1) is bit_width(I_n - 1): the smallest b with

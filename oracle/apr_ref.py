@@ -20,7 +20,7 @@ Alg. 5 in the order the paper states them:
   stop when no mode took an update step in this outer iteration.
 
 Readings (the paper gives no values and leaves one norm unnamed; each is also
-listed in DESIGN.md):
+restated in the design notes):
 
 * |min(B, E - Phi)| is the largest absolute entry of the elementwise minimum
   (the KKT violation of the Poisson subproblem).

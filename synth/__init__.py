@@ -8,7 +8,7 @@ Every generator is a pure function of its arguments and a seed (numpy PCG64).
 Coordinates are 0-based uint32 arrays laid out structure-of-arrays
 ``coords[nmodes, nnz]``; values are float32 ``vals[nnz]``.
 
-Distributions (the recipe is restated in the design doc):
+Distributions:
 
 * ``uniform``  -- ``Generator.integers(0, I)``.
 * ``zipf s``   -- bounded Zipf on {0..I-1}, p(k) proportional to (k+1)^-s,
@@ -45,8 +45,10 @@ class TensorSpec:
     permute_hot: bool = True             # scatter Zipf ranks by a permutation
 
 
-# The four single-tensor workloads. Index 0 is the small case an oracle
-# finishes in seconds; index 1 is the headline configuration.
+# The four single-tensor workloads, named below by what they are: a small
+# uniform 3-mode tensor the oracle finishes in seconds, the 1e8-nonzero Zipf
+# 3-mode tensor of the headline measurement, a 2e8-nonzero 4-mode count
+# tensor, and a 1.5e8-nonzero 5-mode Zipf tensor with 128-bit positions.
 CONFIGS: List[TensorSpec] = [
     TensorSpec("uniform3d_1000x800x600_1e5_r16", (1000, 800, 600), 100_000,
                ("uniform",) * 3, "uniform01", 16, distinct=True, seed=BASE_SEED + 0),
@@ -58,6 +60,8 @@ CONFIGS: List[TensorSpec] = [
     TensorSpec("zipf5d_2Mx100kx10kx1000x50_1.5e8_r64", (2_000_000, 100_000, 10_000, 1000, 50),
                150_000_000, ("zipf:1.1",) * 5, "uniform01", 64, seed=BASE_SEED + 3),
 ]
+
+UNIFORM3D, ZIPF3D, COUNT4D, ZIPF5D = CONFIGS
 
 
 def scaled(spec: TensorSpec, nnz: int, dims: Optional[Sequence[int]] = None,

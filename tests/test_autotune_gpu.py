@@ -16,9 +16,10 @@ def _built():
     gu.ensure_built()
 
 
-@pytest.mark.parametrize("cfg,nnz,R", [(2, 1_000_000, 16), (1, 1_000_000, 32), (3, 300_000, 64)])
-def test_autotuned_plans_keep_parity(cfg, nnz, R):
-    spec = synth.scaled(synth.CONFIGS[cfg], nnz)
+@pytest.mark.parametrize("name,nnz,R", [("COUNT4D", 1_000_000, 16), ("ZIPF3D", 1_000_000, 32),
+                                         ("ZIPF5D", 300_000, 64)])
+def test_autotuned_plans_keep_parity(name, nnz, R):
+    spec = synth.scaled(getattr(synth, name), nnz)
     coords, vals = synth.generate(spec)
     t = gu.encode(coords, vals, spec.dims)
     A = gu.rand_factors(spec.dims, R, 9)

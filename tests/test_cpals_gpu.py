@@ -25,7 +25,7 @@ def _oracle_cpals(coords, vals, dims, init, iters, tol=0.0):
 
 @pytest.mark.parametrize("R", [4, 8, 16, 32, 64])
 def test_fit_trajectory_matches_oracle(R):
-    spec = synth.scaled(synth.CONFIGS[0], 20_000, dims=(200, 160, 120))
+    spec = synth.scaled(synth.UNIFORM3D, 20_000, dims=(200, 160, 120))
     coords, vals = synth.generate(spec)
     init = gu.rand_factors(spec.dims, R, 3)
     ref = _oracle_cpals(coords, vals, spec.dims, init, iters=6)
@@ -42,7 +42,7 @@ def test_fit_trajectory_matches_oracle(R):
 def test_fit_trajectory_zipf_skewed():
     """Zipf heads make the columns of M nearly collinear in early iterations;
     the fit and lambda must still follow the fp64 oracle."""
-    spec = synth.scaled(synth.CONFIGS[1], 300_000, dims=(200_000, 40_000, 5_000))
+    spec = synth.scaled(synth.ZIPF3D, 300_000, dims=(200_000, 40_000, 5_000))
     coords, vals = synth.generate(spec)
     R = 16
     init = gu.rand_factors(spec.dims, R, 11)
@@ -75,7 +75,7 @@ def test_exact_low_rank_recovered():
 
 
 def test_tol_stops_early_and_host_factors_match_device():
-    spec = synth.scaled(synth.CONFIGS[0], 10_000, dims=(100, 90, 80))
+    spec = synth.scaled(synth.UNIFORM3D, 10_000, dims=(100, 90, 80))
     coords, vals = synth.generate(spec)
     init = gu.rand_factors(spec.dims, 8, 5)
     t = gu.encode(coords, vals, spec.dims)

@@ -103,7 +103,7 @@ def test_partition_counts(L):
 
 
 def test_zipf_skewed_and_hot_rows():
-    spec = synth.scaled(synth.CONFIGS[1], 1_000_000)
+    spec = synth.scaled(synth.ZIPF3D, 1_000_000)
     coords, vals = synth.generate(spec)
     t, ref = _check(coords, vals, spec.dims)
     for n, I in enumerate(spec.dims):

@@ -49,7 +49,7 @@ def _run_modes(coords, vals, dims, R, variant=0, cpl=0, bf16=False, seed=0, mode
 @pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("cpl", [4, 8, 16])
 def test_uniform_3d_all_modes(variant, cpl):
-    spec = synth.CONFIGS[0]
+    spec = synth.UNIFORM3D
     coords, vals = synth.generate(spec)
     _run_modes(coords, vals, spec.dims, spec.rank, variant=variant, cpl=cpl, seed=1)
 
@@ -64,14 +64,14 @@ def test_ranks(R, one_thread):
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("cpl", [4, 16])
 def test_bf16_factors(variant, cpl):
-    spec = synth.CONFIGS[0]
+    spec = synth.UNIFORM3D
     coords, vals = synth.generate(spec)
     _run_modes(coords, vals, spec.dims, 16, variant=variant, cpl=cpl, bf16=True, seed=2)
 
 
 @pytest.mark.parametrize("cpl", [4, 64])
 def test_five_modes_two_word_positions(cpl):
-    spec = synth.scaled(synth.CONFIGS[3], 300_000)
+    spec = synth.scaled(synth.ZIPF5D, 300_000)
     coords, vals = synth.generate(spec)
     _run_modes(coords, vals, spec.dims, 64, cpl=cpl, seed=4)
     _run_modes(coords, vals, spec.dims, 64, cpl=cpl, bf16=True, seed=4)
@@ -79,7 +79,7 @@ def test_five_modes_two_word_positions(cpl):
 
 @pytest.mark.parametrize("cpl", [4, 8, 32])
 def test_zipf_hot_rows(cpl):
-    spec = synth.scaled(synth.CONFIGS[1], 2_000_000)
+    spec = synth.scaled(synth.ZIPF3D, 2_000_000)
     coords, vals = synth.generate(spec)
     _run_modes(coords, vals, spec.dims, 32, variant=1, seed=5, cpl=cpl)
 
@@ -93,7 +93,7 @@ def test_six_and_two_modes_generic_kernel():
 
 
 def test_count_tensor_small_modes_pull():
-    spec = synth.scaled(synth.CONFIGS[2], 2_000_000)
+    spec = synth.scaled(synth.COUNT4D, 2_000_000)
     coords, vals = synth.generate(spec)
     t, _ = _run_modes(coords, vals, spec.dims, 16, seed=6)
     assert t.get_mode_plan(3, 16)[0] == 3   # AUTO: the stored output-oriented order
@@ -183,15 +183,15 @@ def _full_size_rows(spec, R, bf16=False, nrand=192, nhot=64, seed=10):
 
 @pytest.mark.slow
 def test_full_size_zipf3d():
-    _full_size_rows(synth.CONFIGS[1], 32)
+    _full_size_rows(synth.ZIPF3D, 32)
 
 
 @pytest.mark.slow
 def test_full_size_count4d():
-    _full_size_rows(synth.CONFIGS[2], 16)
+    _full_size_rows(synth.COUNT4D, 16)
 
 
 @pytest.mark.slow
 def test_full_size_zipf5d_fp32_and_bf16():
-    _full_size_rows(synth.CONFIGS[3], 64)
-    _full_size_rows(synth.CONFIGS[3], 64, bf16=True)
+    _full_size_rows(synth.ZIPF5D, 64)
+    _full_size_rows(synth.ZIPF5D, 64, bf16=True)

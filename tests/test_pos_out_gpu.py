@@ -94,7 +94,7 @@ def test_output_mttkrp_segment_counts_and_modes(L):
 @pytest.mark.parametrize("cpl", [4, 8])
 def test_output_mttkrp_bf16(cpl):
     import torch
-    spec = synth.CONFIGS[0]
+    spec = synth.UNIFORM3D
     coords, vals = synth.generate(spec)
     t = gu.encode(coords, vals, spec.dims)
     A = gu.rand_factors(spec.dims, 16, 2)

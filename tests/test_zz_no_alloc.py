@@ -27,7 +27,7 @@ def _built():
 def test_noalloc_matches_regular_entry_point_on_two_calls():
     import torch
     import paper_2403_06348_gb300 as alto
-    spec = synth.scaled(synth.CONFIGS[2], 400_000)   # count tensor: 200- and 24-row modes
+    spec = synth.scaled(synth.COUNT4D, 400_000)   # count tensor: 200- and 24-row modes
     coords, vals = synth.generate(spec)
     t = gu.encode(coords, vals, spec.dims)
     R = 16
@@ -46,7 +46,7 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
 def test_noalloc_rejects_what_it_cannot_do():
     import torch
     import paper_2403_06348_gb300 as alto
-    spec = synth.scaled(synth.CONFIGS[2], 400_000)
+    spec = synth.scaled(synth.COUNT4D, 400_000)
     coords, vals = synth.generate(spec)
     t = gu.encode(coords, vals, spec.dims)
     R = 64
