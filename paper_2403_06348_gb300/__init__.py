@@ -211,13 +211,17 @@ def alto_encode(coords, vals, dims: Sequence[int], stream=None, allocator=None) 
     keep = []
 
     def prep(x, np_dtype):
+        torch = None
+        if not isinstance(x, np.ndarray):
+            torch = _torch()
+            if x.device.type == "cpu":
+                x = x.numpy()
         if isinstance(x, np.ndarray):
+            if np_dtype == np.uint32 and x.dtype == np.int32:
+                # same bits: no host copy (a pinned buffer stays pinned); a
+                # negative coordinate fails the library's range check
+                x = x.view(np.uint32)
             a = np.ascontiguousarray(x, dtype=np_dtype)
-            keep.append(a)
-            return a.ctypes.data
-        torch = _torch()
-        if x.device.type == "cpu":
-            a = np.ascontiguousarray(x.numpy(), dtype=np_dtype)
             keep.append(a)
             return a.ctypes.data
         x = x.contiguous()
