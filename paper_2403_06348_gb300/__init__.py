@@ -205,23 +205,26 @@ def _ptr(x) -> int:
 # C-named entry points (argument marshalling only)
 # ---------------------------------------------------------------------------
 
+def host_array(x, np_dtype) -> np.ndarray:
+    """A host array (numpy or CPU tensor) as a C-contiguous ``np_dtype`` array,
+    without a copy where the bits already fit: int32 coordinates are read as
+    uint32 in place, so a pinned buffer reaches the library as pinned memory
+    (a negative coordinate then fails the library's range check)."""
+    if not isinstance(x, np.ndarray):
+        x = x.numpy()
+    if np_dtype == np.uint32 and x.dtype == np.int32:
+        x = x.view(np.uint32)
+    return np.ascontiguousarray(x, dtype=np_dtype)
+
+
 def alto_encode(coords, vals, dims: Sequence[int], stream=None, allocator=None) -> "AltoTensor":
     """Encode a COO tensor. ``coords`` is [nmodes, nnz] uint32/int32 and ``vals``
     [nnz] float32, each a CUDA tensor or a (host) numpy array / CPU tensor."""
     keep = []
 
     def prep(x, np_dtype):
-        torch = None
-        if not isinstance(x, np.ndarray):
-            torch = _torch()
-            if x.device.type == "cpu":
-                x = x.numpy()
-        if isinstance(x, np.ndarray):
-            if np_dtype == np.uint32 and x.dtype == np.int32:
-                # same bits: no host copy (a pinned buffer stays pinned); a
-                # negative coordinate fails the library's range check
-                x = x.view(np.uint32)
-            a = np.ascontiguousarray(x, dtype=np_dtype)
+        if isinstance(x, np.ndarray) or x.device.type == "cpu":
+            a = host_array(x, np_dtype)
             keep.append(a)
             return a.ctypes.data
         x = x.contiguous()

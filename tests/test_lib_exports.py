@@ -69,3 +69,25 @@ def test_product_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", text).replace("oracles", ""), f
+
+
+def test_host_coordinates_are_passed_without_a_copy():
+    """int32 host coordinates reach the library as the same memory (read as
+    uint32), so a pinned buffer stays pinned; other dtypes are converted."""
+    import numpy as np
+    import torch
+    import paper_2403_06348_gb300 as alto
+    c32 = np.arange(12, dtype=np.int32).reshape(3, 4)
+    a = alto.host_array(c32, np.uint32)
+    assert a.dtype == np.uint32 and np.shares_memory(a, c32)
+    np.testing.assert_array_equal(a, c32.astype(np.uint32))
+    t = torch.arange(12, dtype=torch.int32).reshape(3, 4)
+    b = alto.host_array(t, np.uint32)
+    assert b.dtype == np.uint32 and b.ctypes.data == t.data_ptr()
+    neg = alto.host_array(np.array([[-1]], dtype=np.int32), np.uint32)
+    assert neg[0, 0] == 0xFFFFFFFF            # out of range for any mode: rejected on the device
+    c64 = np.arange(6, dtype=np.int64).reshape(2, 3)
+    d = alto.host_array(c64, np.uint32)
+    assert d.dtype == np.uint32 and not np.shares_memory(d, c64)
+    v = np.ones(5, dtype=np.float32)
+    assert np.shares_memory(alto.host_array(v, np.float32), v)
