@@ -168,11 +168,17 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint64_t *__
   hist[threadIdx.x] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)t * kSortTile;
-#pragma unroll 4
+  // all of the thread's digits first (16 loads in flight), then the counts
+  uint32_t dig[kSortItems];
+#pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint64_t x = base + (uint64_t)i * kSortThreads + threadIdx.x;
-    const bool valid = x < nnz;
-    const uint32_t d = valid ? (uint32_t)((keys[x * KW + word] >> shift) & 0xFFu) : kRadix;
+    dig[i] = x < nnz ? (uint32_t)((keys[x * KW + word] >> shift) & 0xFFu) : kRadix;
+  }
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t d = dig[i];
+    const bool valid = d < kRadix;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
   }
@@ -290,6 +296,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
   float v[kSortItems];
   uint32_t rank[kSortItems];
   uint32_t dig[kSortItems];
+  // all of the thread's items first (loads in flight together), then the ranks
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const uint64_t x = tile_base + (uint64_t)warp * (32 * kSortItems) + r * 32 + lane;
@@ -297,6 +304,11 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
 #pragma unroll
     for (int w = 0; w < KW; ++w) k[r][w] = valid ? keys_in[x * KW + w] : 0ull;
     v[r] = valid ? vals_in[x] : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const uint64_t x = tile_base + (uint64_t)warp * (32 * kSortItems) + r * 32 + lane;
+    const bool valid = x < nnz;
     const uint64_t kd = (KW == 2 && word) ? k[r][KW - 1] : k[r][0];
     const uint32_t d = valid ? (uint32_t)((kd >> shift) & 0xFFu) : kRadix;
     dig[r] = d;
