@@ -122,7 +122,9 @@ typedef struct alto_mode_plan {
                          nonzero one thread, which walks its rows in 8-column
                          chunks; 0 = library default. OUTPUT uses 4 or 8
                          (larger requests take 8, or 4 when R = 4)               */
-  int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit             */
+  int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit; OUTPUT:
+                         resolved to the hot rows its long runs may stage
+                         (set by the library, up to 256)                        */
 } alto_mode_plan;
 
 /* ---------------------------------------------------------------------------
