@@ -191,17 +191,15 @@ def kernel_src_sha():
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes_per_mode(coords, dims, R, key_bytes, fbytes=4, order_bytes=None):
+def algorithmic_bytes_per_mode(coords, dims, R, key_bytes, fbytes=4):
     """M*(key+value bytes) + sum_{m!=n} D_m*R*fbytes + I_n*R*4, D_m = distinct
-    rows; plus M*order_bytes[n] for a mode walked through its stored order."""
+    rows of mode m (the roofline model of one mode-n MTTKRP)."""
     M = coords.shape[1]
     D = [int(np.count_nonzero(np.bincount(coords[m], minlength=dims[m]))) for m in range(len(dims))]
     out = []
     for n in range(len(dims)):
         b = M * (key_bytes + 4) + sum(D[m] * R * fbytes for m in range(len(dims)) if m != n)
         b += dims[n] * R * 4
-        if order_bytes is not None:
-            b += M * order_bytes[n]
         out.append(b)
     return out, D
 
@@ -364,8 +362,10 @@ def run_ours(args):
     kw = prof.get("_kw", 1)
     used = prof.get("_plans") or []
     outorder = [len(used) > n and used[n][0] == 3 for n in range(N)]
-    bytes_per_mode, distinct = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw,
-                                                          order_bytes=[4 if o else 0 for o in outorder])
+    # the roofline model's bytes: the nonzero stream once, the distinct input
+    # rows once, the output once; the same for every plan (a plan's extra
+    # traffic, such as a stored order, is overhead, not algorithmic bytes)
+    bytes_per_mode, distinct = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw)
     kernel = ("mttkrp_out_kernel" if all(outorder) else
               "mttkrp_kernel" if not any(outorder) else "mttkrp_out_kernel + mttkrp_kernel")
     n_mttkrp, ms_mttkrp = prof.get("mttkrp", (0, 0.0))

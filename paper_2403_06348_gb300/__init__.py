@@ -205,15 +205,22 @@ def _ptr(x) -> int:
 # C-named entry points (argument marshalling only)
 # ---------------------------------------------------------------------------
 
-def host_array(x, np_dtype) -> np.ndarray:
+def host_array(x, np_dtype, what: str = "array") -> np.ndarray:
     """A host array (numpy or CPU tensor) as a C-contiguous ``np_dtype`` array,
     without a copy where the bits already fit: int32 coordinates are read as
     uint32 in place, so a pinned buffer reaches the library as pinned memory
-    (a negative coordinate then fails the library's range check)."""
+    (a negative coordinate then fails the library's range check). Wider or
+    signed integer coordinates are converted only when every value fits
+    uint32; otherwise ValueError (a silent wrap would encode another tensor)."""
     if not isinstance(x, np.ndarray):
         x = x.numpy()
     if np_dtype == np.uint32 and x.dtype == np.int32:
         x = x.view(np.uint32)
+    if np_dtype == np.uint32 and x.dtype != np.uint32:
+        if not np.issubdtype(x.dtype, np.integer):
+            raise TypeError(f"{what}: host array of dtype {x.dtype}; expected integers")
+        if x.size and (int(x.min()) < 0 or int(x.max()) > 0xFFFFFFFF):
+            raise ValueError(f"{what}: values outside [0, 2^32) cannot be coordinates")
     return np.ascontiguousarray(x, dtype=np_dtype)
 
 
@@ -222,11 +229,20 @@ def alto_encode(coords, vals, dims: Sequence[int], stream=None, allocator=None) 
     [nnz] float32, each a CUDA tensor or a (host) numpy array / CPU tensor."""
     keep = []
 
-    def prep(x, np_dtype):
+    def prep(x, np_dtype, what):
         if isinstance(x, np.ndarray) or x.device.type == "cpu":
-            a = host_array(x, np_dtype)
+            a = host_array(x, np_dtype, what)
             keep.append(a)
             return a.ctypes.data
+        # device memory goes to the library as a raw pointer, read as uint32
+        # coordinates / float32 values: any other element type would be
+        # misread (an int64 coordinate's high word as the next coordinate)
+        torch = _torch()
+        ok = (torch.int32, getattr(torch, "uint32", torch.int32)) if np_dtype == np.uint32 \
+            else (torch.float32,)
+        if x.dtype not in ok:
+            raise TypeError(f"{what}: CUDA tensor of dtype {x.dtype}; expected "
+                            f"{' or '.join(str(d) for d in ok)}")
         x = x.contiguous()
         keep.append(x)
         return x.data_ptr()
@@ -235,13 +251,22 @@ def alto_encode(coords, vals, dims: Sequence[int], stream=None, allocator=None) 
     if hasattr(coords, "shape") and coords.shape[0] != nmodes:
         raise ValueError("coords must be [nmodes, nnz]")
     nnz = int(coords.shape[1]) if nmodes else 0
-    cp = prep(coords, np.uint32)
-    vp = prep(vals, np.float32)
+    cp = prep(coords, np.uint32, "coords")
+    vp = prep(vals, np.float32, "vals")
     dims_a = (ctypes.c_uint64 * nmodes)(*[int(d) for d in dims])
     h = ctypes.c_void_p()
     al = ctypes.byref(allocator) if allocator is not None else None
     _check(lib().alto_encode(cp, vp, dims_a, nmodes, nnz, al, _stream_ptr(stream), ctypes.byref(h)))
     return AltoTensor(h, tuple(int(d) for d in dims), nnz, allocator)
+
+
+def _factor_dtype(factors, mode: int) -> int:
+    """ALTO_BF16 when the input factors are bfloat16 tensors, else ALTO_F32."""
+    for m, f in enumerate(factors):
+        if m != mode and f is not None and getattr(f, "dtype", None) is not None \
+                and str(f.dtype) == "torch.bfloat16":
+            return ALTO_BF16
+    return ALTO_F32
 
 
 def alto_mttkrp(t: "AltoTensor", mode: int, factors, R: int, out, dtype: int = ALTO_F32,
@@ -251,10 +276,13 @@ def alto_mttkrp(t: "AltoTensor", mode: int, factors, R: int, out, dtype: int = A
                              _stream_ptr(stream)))
 
 
-def alto_mttkrp_noalloc(t: "AltoTensor", mode: int, factors, R: int, out, dtype: int = ALTO_F32,
+def alto_mttkrp_noalloc(t: "AltoTensor", mode: int, factors, R: int, out, dtype: Optional[int] = None,
                         stream=None) -> None:
     """Pull-variant MTTKRP that allocates nothing (scratch in the library's fixed
-    device array); the mode's pull lists must exist (see include/alto.h)."""
+    device array); the mode's pull lists must exist (see include/alto.h).
+    ``dtype`` defaults to the factors' element type (ALTO_BF16 for bfloat16)."""
+    if dtype is None:
+        dtype = _factor_dtype(factors, mode)
     arr = (ctypes.c_void_p * t.nmodes)(*[_ptr(f) for f in factors])
     _check(lib().alto_mttkrp_noalloc(t.handle, int(mode), arr, int(dtype), int(R), _ptr(out),
                                      _stream_ptr(stream)))
@@ -474,12 +502,7 @@ class AltoTensor:
                stream=None):
         torch = _torch()
         R = int(R if R is not None else factors[(mode + 1) % self.nmodes].shape[1])
-        code = ALTO_F32
-        for m, f in enumerate(factors):
-            if m != mode and f is not None and f.dtype == torch.bfloat16:
-                code = ALTO_BF16
-        if dtype is not None:
-            code = dtype
+        code = dtype if dtype is not None else _factor_dtype(factors, mode)
         if out is None:
             rows = self.dims[mode] if 0 <= mode < self.nmodes else 1  # the C call rejects bad modes
             out = torch.empty((rows, R), dtype=torch.float32, device="cuda")

@@ -527,7 +527,7 @@ alto_status set_pos_out(alto_tensor *h, int n, uint64_t L, cudaStream_t s) {
 
 alto_status check_handle(alto_tensor *h) {
   if (!h) return fail(ALTO_ERR_INVALID_ARG, "null handle");
-  return ALTO_OK;
+  return check_device(h);
 }
 
 alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bool bf16, int R,
@@ -730,6 +730,15 @@ alto_status phi_impl(alto_tensor *h, int mode, const float *const *A, const floa
 }
 
 }  // namespace
+
+alto_status alto::check_device(const alto_tensor *h) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != h->device)
+    return fail(ALTO_ERR_INVALID_ARG, "handle encoded on device %d, called with device %d current",
+                h->device, dev);
+  return ALTO_OK;
+}
 
 alto_status alto::repartition(alto_tensor *h, uint64_t L, cudaStream_t s) {
   return run_partition(h, L, s);

@@ -561,6 +561,7 @@ void alto_batch_free(alto_batch_t b) {
 
 alto_status alto_batch_prepare(alto_handle_t h, int R) {
   if (!h) return fail(ALTO_ERR_INVALID_ARG, "null handle");
+  if (check_device(h) != ALTO_OK) return ALTO_ERR_INVALID_ARG;  // message set by check_device
   if (!(R == 4 || R == 8 || R == 16 || R == 32 || R == 64))
     return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
   cudaStream_t hs = h->stream;
@@ -578,6 +579,7 @@ alto_status alto_batch_prepare(alto_handle_t h, int R) {
 alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, double tol,
                            const float *const *factors, int *slot_out) {
   if (!b || !h) return fail(ALTO_ERR_INVALID_ARG, "null batch or handle");
+  if (check_device(h) != ALTO_OK) return ALTO_ERR_INVALID_ARG;  // message set by check_device
   if (!(R == 4 || R == 8 || R == 16 || R == 32 || R == 64))
     return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
   if (iters < 1) return fail(ALTO_ERR_INVALID_ARG, "iters must be >= 1");

@@ -365,6 +365,9 @@ extern "C" alto_status alto_mttkrp_grouped(int n, const alto_handle_t *hs, const
   for (int i = 0; i < n; ++i) {
     alto_tensor *h = hs[i];
     if (!h) return fail(ALTO_ERR_INVALID_ARG, "problem %d: null handle", i);
+    if (check_device(h) != ALTO_OK)
+      return fail(ALTO_ERR_INVALID_ARG, "problem %d: handle encoded on device %d, not the current one", i,
+                  h->device);
     const int mode = modes[i], R = Rs[i];
     if (mode < 0 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "problem %d: mode %d", i, mode);
     if (!(R == 4 || R == 8 || R == 16 || R == 32 || R == 64))

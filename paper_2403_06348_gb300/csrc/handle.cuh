@@ -55,6 +55,10 @@ namespace alto {
 void *dalloc(alto_tensor *h, size_t bytes, cudaStream_t s);
 void dfree(alto_tensor *h, void *p, size_t bytes, cudaStream_t s);
 
+// ALTO_ERR_INVALID_ARG unless the current device is the one h was encoded on
+// (its buffers, plans and tables live there).
+alto_status check_device(const alto_tensor *h);
+
 // Re-partitions the handle into L segments (Section IV-A) on stream s; waits
 // for s (the interval lengths come back to the host).
 alto_status repartition(alto_tensor *h, uint64_t L, cudaStream_t s);

@@ -51,6 +51,8 @@ using namespace alto;
 extern "C" alto_status alto_mttkrp_noalloc(alto_handle_t h, int mode, const void *const *factors,
                                            alto_dtype fdtype, int R, float *out, void *stream) {
   if (!h) return fail(ALTO_ERR_INVALID_ARG, "null handle");
+  alto_status st = check_device(h);
+  if (st != ALTO_OK) return st;
   if (mode < 0 || mode >= h->N) return fail(ALTO_ERR_INVALID_ARG, "mode %d out of range", mode);
   if (!(R == 4 || R == 8 || R == 16 || R == 32 || R == 64))
     return fail(ALTO_ERR_UNSUPPORTED, "rank %d not in {4,8,16,32,64}", R);
@@ -85,7 +87,7 @@ extern "C" alto_status alto_mttkrp_noalloc(alto_handle_t h, int mode, const void
                 "mode %d at rank %d needs %llu floats of scratch; the fixed scratch holds %llu",
                 mode, R, (unsigned long long)need, (unsigned long long)kNoAllocScratchFloats);
   float *scratch = nullptr;
-  alto_status st = scratch_address(&scratch);
+  st = scratch_address(&scratch);
   if (st != ALTO_OK) return st;
 
   MttkrpArgs a{};

@@ -128,3 +128,20 @@ def test_too_many_bits_unsupported():
     with pytest.raises(alto.AltoError) as e:
         gu.encode(np.zeros((5, 4), np.uint32), np.ones(4, np.float32), (1 << 26,) * 5)
     assert e.value.status == -4
+
+
+def test_device_inputs_of_the_wrong_dtype_are_refused():
+    """CUDA tensors reach the library as raw pointers read as uint32 / float32;
+    int64 coordinates or float64 values would be misread, so the binding
+    refuses them before any call."""
+    import torch
+    import paper_2403_06348_gb300 as alto
+    c = torch.zeros((3, 10), dtype=torch.int64, device="cuda")
+    v = torch.ones(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(TypeError):
+        alto.alto_encode(c, v, (4, 4, 4))
+    with pytest.raises(TypeError):
+        alto.alto_encode(c.to(torch.int32), v.double(), (4, 4, 4))
+    t = alto.alto_encode(c.to(torch.int32), v, (4, 4, 4))
+    assert t.nnz == 10
+    t.free()

@@ -91,3 +91,22 @@ def test_host_coordinates_are_passed_without_a_copy():
     assert d.dtype == np.uint32 and not np.shares_memory(d, c64)
     v = np.ones(5, dtype=np.float32)
     assert np.shares_memory(alto.host_array(v, np.float32), v)
+
+
+def test_coordinates_that_do_not_fit_uint32_are_refused():
+    """Host coordinates of a wider or signed type are converted only when every
+    value fits uint32; otherwise the binding raises instead of wrapping them
+    into another tensor (nothing reaches the library)."""
+    import numpy as np
+    import paper_2403_06348_gb300 as alto
+    big = np.array([[1, 1 << 32]], dtype=np.int64)
+    with pytest.raises(ValueError):
+        alto.host_array(big, np.uint32, "coords")
+    with pytest.raises(ValueError):
+        alto.host_array(np.array([[-3]], dtype=np.int64), np.uint32, "coords")
+    with pytest.raises(TypeError):
+        alto.host_array(np.array([[1.5]]), np.uint32, "coords")
+    with pytest.raises(ValueError):
+        alto.alto_encode(np.array([[0, 1 << 33]], dtype=np.int64), np.ones(2, np.float32), (4,))
+    ok = alto.host_array(np.array([[0, (1 << 32) - 1]], dtype=np.int64), np.uint32, "coords")
+    assert ok.dtype == np.uint32 and int(ok[0, 1]) == (1 << 32) - 1

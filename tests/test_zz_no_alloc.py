@@ -2,21 +2,24 @@
 the library allocate device memory while they run.
 
 Its partials live in a fixed device array inside the library instead of a
-buffer the library allocates, so its results must equal those of the regular
-entry point (same tolerance as every fp32 MTTKRP test: 1e-5 row-relative),
-call after call: the array keeps the previous call's contents. This file is
-named to be collected last.
+buffer the library allocates. Its results must match the fp64 oracle within
+the bar of every MTTKRP test (1e-5 row-relative for fp32 factors, 1e-2 for
+bf16 factors against the oracle on the original fp32 factors), and the
+regular entry point within the same bar, call after call: the array keeps the
+previous call's contents. This file is named to be collected last.
 """
 import numpy as np
 import pytest
 
 import synth
 from oracle import alto_ref as ar
+from oracle import cref
 from tests import gpu_util as gu
 
 pytestmark = pytest.mark.gpu
 
 TOL_F32 = 1e-5
+TOL_BF16 = 1e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -24,23 +27,31 @@ def _built():
     gu.ensure_built()
 
 
-def test_noalloc_matches_regular_entry_point_on_two_calls():
+@pytest.mark.parametrize("bf16", [False, True])
+def test_noalloc_matches_oracle_and_regular_entry_point_on_two_calls(bf16):
     import torch
     import paper_2403_06348_gb300 as alto
     spec = synth.scaled(synth.COUNT4D, 400_000)   # count tensor: 200- and 24-row modes
     coords, vals = synth.generate(spec)
     t = gu.encode(coords, vals, spec.dims)
     R = 16
-    A = gu.gpu_factors(gu.rand_factors(spec.dims, R, 3))
+    A = gu.rand_factors(spec.dims, R, 3)
+    Ad = gu.gpu_factors(A, torch.bfloat16 if bf16 else torch.float32)
+    tol = TOL_BF16 if bf16 else TOL_F32
     for mode in (2, 3):
+        want = cref.mttkrp(coords, vals, spec.dims, A, mode, nthreads=4)   # fp64 oracle
         t.set_mode_plan(mode, alto.VARIANT_PULL)
-        ref = t.mttkrp(mode, A, R).cpu().numpy()      # regular entry point; builds the pull lists
+        regular = t.mttkrp(mode, Ad, R).cpu().numpy()   # regular entry point; builds the pull lists
+        err, bad_zero = ar.row_relative_error(regular, want)
+        assert bad_zero == 0 and err <= tol, ("regular", mode, err)
         for call in range(2):
             out = torch.full((spec.dims[mode], R), float("nan"), device="cuda")
-            alto.alto_mttkrp_noalloc(t, mode, A, R, out)
+            alto.alto_mttkrp_noalloc(t, mode, Ad, R, out)   # element type taken from the factors
             got = out.cpu().numpy()
-            err, bad_zero = ar.row_relative_error(got, ref)
-            assert bad_zero == 0 and err <= TOL_F32, (mode, call, err)
+            err, bad_zero = ar.row_relative_error(got, want)
+            assert bad_zero == 0 and err <= tol, ("oracle", mode, call, err)
+            err, bad_zero = ar.row_relative_error(got, regular)
+            assert bad_zero == 0 and err <= tol, ("regular entry point", mode, call, err)
 
 
 def test_noalloc_rejects_what_it_cannot_do():
