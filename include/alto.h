@@ -70,6 +70,19 @@ typedef enum alto_dtype { ALTO_F32 = 0, ALTO_BF16 = 1 } alto_dtype;
  *          The stored order holds, per nonzero, its ordered position (4
  *          bytes), its line position (8 * key_words bytes) and its value (4
  *          bytes): pos_out and val_out of Alg. 4, read as one stream.
+ *  TILED:  the output-oriented traversal done inside each tile of 1024
+ *          consecutive nonzeros of the one ALTO copy, with no stored order:
+ *          the tile arrives in shared memory by a bulk asynchronous copy, is
+ *          decoded once, and its nonzeros are grouped by output row (one bin
+ *          per hot row of the mode, one for the rest) before groups of
+ *          threads walk contiguous pieces of it, summing runs of equal row in
+ *          registers. Runs of the most frequent rows go to shared memory
+ *          (flushed once per CTA), of the next most frequent rows to a few
+ *          fp32 replicas that a second small kernel adds into the output,
+ *          of all other rows straight to the output with vector atomics.
+ *          Needs dims[mode] <= 2^31 (else ATOMIC). hot_rows resolves to the
+ *          rows staged in shared memory.
+ *  TILED_LINE: TILED without the grouping (each tile in line order).
  *  AUTO:   OUTPUT (measured faster on GB300 than PULL and ATOMIC for modes
  *          of any reuse); if the order cannot be allocated (or nnz is too
  *          large for it), the paper's rule: PULL when the fiber reuse
@@ -80,7 +93,9 @@ typedef enum alto_variant {
   ALTO_VARIANT_AUTO = 0,
   ALTO_VARIANT_ATOMIC = 1,
   ALTO_VARIANT_PULL = 2,
-  ALTO_VARIANT_OUTPUT = 3
+  ALTO_VARIANT_OUTPUT = 3,
+  ALTO_VARIANT_TILED = 4,
+  ALTO_VARIANT_TILED_LINE = 5
 } alto_variant;
 
 /* Optional device-memory allocator. alloc returns a device pointer aligned to
@@ -120,11 +135,13 @@ typedef struct alto_mode_plan {
                          nonzero over R/cols_per_lane threads ("threads per
                          nonzero"); cols_per_lane == R (R >= 8) gives each
                          nonzero one thread, which walks its rows in 8-column
-                         chunks; 0 = library default. OUTPUT uses 4 or 8
-                         (larger requests take 8, or 4 when R = 4)               */
+                         chunks; 0 = library default. OUTPUT, TILED and
+                         TILED_LINE use 4 or 8 (larger requests and 0 take 8,
+                         or 4 when R = 4)                                        */
   int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit; OUTPUT:
                          resolved to the hot rows its long runs may stage
-                         (set by the library, up to 256)                        */
+                         (set by the library, up to 256); TILED, TILED_LINE:
+                         resolved to the hot rows staged in shared memory      */
 } alto_mode_plan;
 
 /* ---------------------------------------------------------------------------

@@ -25,6 +25,7 @@ ALTO_MAX_MODES = 8
 ALTO_MAX_HOT = 4096
 ALTO_F32, ALTO_BF16 = 0, 1
 VARIANT_AUTO, VARIANT_ATOMIC, VARIANT_PULL, VARIANT_OUTPUT = 0, 1, 2, 3
+VARIANT_TILED, VARIANT_TILED_LINE = 4, 5
 
 STATUS_NAMES = {0: "ALTO_OK", -1: "ALTO_ERR_INVALID_ARG", -2: "ALTO_ERR_OOM", -3: "ALTO_ERR_CUDA",
                 -4: "ALTO_ERR_UNSUPPORTED", -5: "ALTO_ERR_COORD_RANGE", -6: "ALTO_ERR_NOT_SPD",

@@ -428,8 +428,48 @@ alto_status out_staging(alto_tensor *h, int n, int R, MttkrpArgs &a, size_t *sme
   return ALTO_OK;
 }
 
+// In-tile output-oriented traversal (TILED): the mode's most frequent rows
+// get bins (at most kTileBins); as many of them as fit two CTAs per SM are
+// staged in shared memory, the rest go to the warm replicas.
+constexpr int kTileBins = 1024;
+
+int hbits_for(int k) {
+  int hb = 1;
+  while ((1 << hb) < 2 * std::max(k, 1)) ++hb;
+  return hb;
+}
+
+int tile_bins(const alto_tensor *h, int mode) { return std::min<int>((int)h->nhot[mode], kTileBins); }
+
+int tile_slots(const alto_tensor *h, int mode, int R, int cpl) {
+  const int nb = tile_bins(h, mode);
+  const int hb = hbits_for(nb);
+  static int per_sm = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  }
+  const size_t base = tile_smem_bytes(h->N, h->kw, R, cpl, 0, hb, nb);
+  size_t target = (size_t)per_sm / 2 - 1024;  // two CTAs per SM
+  if (target > mttkrp_smem_limit()) target = mttkrp_smem_limit();
+  if (base >= target) return 0;
+  const size_t k = (target - base) / ((size_t)R * 4);
+  return (int)std::min<size_t>(k, (size_t)nb);
+}
+
+bool tile_variant(int v) { return v == ALTO_VARIANT_TILED || v == ALTO_VARIANT_TILED_LINE; }
+
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   alto_mode_plan p = h->plan[mode];
+  if (tile_variant(p.variant) && h->dims[mode] > 0x80000000ull) p.variant = ALTO_VARIANT_ATOMIC;
+  if (tile_variant(p.variant)) {
+    const bool wide = R >= 8 && (p.cols_per_lane == 0 || p.cols_per_lane >= 8);
+    p.cols_per_lane = wide ? 8 : 4;
+    p.hot_rows = tile_slots(h, mode, R, p.cols_per_lane);
+    *out = p;
+    return ALTO_OK;
+  }
   if (p.cols_per_lane != 4 && p.cols_per_lane != 8 && p.cols_per_lane != 16 &&
       p.cols_per_lane != 32 && p.cols_per_lane != 64)
     p.cols_per_lane = 4;
@@ -590,6 +630,42 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     }
     ProfScope ps(h, ALTO_PROF_MTTKRP, s);
     CUDA_TRY(launch_mttkrp_out(a, p.cols_per_lane, bf16, smem, h->num_sms, s));
+    return ALTO_OK;
+  }
+  if (tile_variant(p.variant)) {
+    if (p.cols_per_lane == 8 && !bf16)
+      for (int m = 0; m < h->N; ++m)
+        if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
+    const int nb = tile_bins(h, mode);
+    const int nslots = std::min(tile_slots(h, mode, R, p.cols_per_lane), nb);
+    const HotTable *tab = nullptr;
+    if ((st = ensure_group_hot(h, mode, nb, s, &tab)) != ALTO_OK) return st;
+    a.htab = tab->htab;
+    a.hbits = tab->hbits;
+    a.nbins = tab->nslots;
+    a.nslots = std::min(nslots, a.nbins);
+    a.slot_rows = h->hot_rows[mode];
+    a.status = h->status_dev;
+    if (a.nbins > a.nslots) {
+      const size_t need = (size_t)kTileWarmReps * (size_t)a.nbins * (size_t)R * sizeof(float);
+      if (h->warm.bytes < need) {
+        dfree(h, h->warm.p, h->warm.bytes, s);
+        h->warm.p = dalloc(h, need, s);
+        h->warm.bytes = h->warm.p ? need : 0;
+        if (!h->warm.p) return fail(ALTO_ERR_OOM, "warm-row replicas of %zu bytes", need);
+        // zero once; every launch leaves the replicas zero again
+        CUDA_TRY(cudaMemsetAsync(h->warm.p, 0, need, s));
+      }
+      a.warm = static_cast<float *>(h->warm.p);
+    }
+    {
+      ProfScope ps(h, ALTO_PROF_ZERO, s);
+      CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
+    }
+    ProfScope ps(h, ALTO_PROF_MTTKRP, s);
+    CUDA_TRY(launch_mttkrp_tile(a, p.cols_per_lane, bf16, p.variant == ALTO_VARIANT_TILED, h->num_sms, s));
+    if (a.nbins > a.nslots)
+      CUDA_TRY(launch_warm_reduce(a.warm, a.slot_rows, a.nslots, a.nbins, R, out, h->num_sms, s));
     return ALTO_OK;
   }
   if (p.variant == ALTO_VARIANT_PULL) {
@@ -980,6 +1056,7 @@ void alto_free(alto_handle_t h) {
     if (h->hot_rows[n]) dfree(h, h->hot_rows[n], ALTO_MAX_HOT * 4, s);
   }
   dfree(h, h->partials.p, h->partials.bytes, s);
+  dfree(h, h->warm.p, h->warm.bytes, s);
   dfree(h, h->keys, h->M * h->kw * 8, s);
   dfree(h, h->vals, h->M * 4, s);
   dfree(h, h->dims_dev, kMaxModes * 8, s);
@@ -1117,7 +1194,7 @@ alto_status alto_set_mode_plan(alto_handle_t h, int mode, const alto_mode_plan *
   alto_status st = check_handle(h);
   if (st != ALTO_OK) return st;
   if (mode < 0 || mode >= h->N || !plan) return fail(ALTO_ERR_INVALID_ARG, "bad mode or plan");
-  if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_OUTPUT)
+  if (plan->variant < ALTO_VARIANT_AUTO || plan->variant > ALTO_VARIANT_TILED_LINE)
     return fail(ALTO_ERR_INVALID_ARG, "unknown variant %d", plan->variant);
   if (plan->cols_per_lane != 0 && plan->cols_per_lane != 4 && plan->cols_per_lane != 8 &&
       plan->cols_per_lane != 16 && plan->cols_per_lane != 32 && plan->cols_per_lane != 64)
@@ -1433,6 +1510,10 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
       if ((flags & ALTO_TUNE_OUTPUT) && L == L0)
         for (int c : cpls)
           if (R % c == 0 && (c == 4 || R >= 8)) cands.push_back(alto_mode_plan{ALTO_VARIANT_OUTPUT, c, 0});
+      if (L == L0 && h->dims[n] <= 0x80000000ull)
+        for (int v : {ALTO_VARIANT_TILED, ALTO_VARIANT_TILED_LINE})
+          for (int c : cpls)
+            if (R % c == 0 && (c == 4 || R >= 8)) cands.push_back(alto_mode_plan{v, c, 0});
       if (cands.empty()) cands.push_back(alto_mode_plan{ALTO_VARIANT_AUTO, 0, -1});
       double bms = 1e300;
       alto_mode_plan bp{};

@@ -138,6 +138,7 @@ struct alto_tensor {
   HotTable group_hot[alto::kMaxModes][5];  // smaller tables for grouped launches, by size
   PullPlan pull[alto::kMaxModes];
   Buf partials;
+  Buf warm;                                 // TILED: warm-row replicas (zero between launches)
   uint32_t *pos_out[alto::kMaxModes] = {};  // stored output-oriented order per mode
   uint64_t *keys_out[alto::kMaxModes] = {}; // line positions in that order [nnz][kw]
   float *vals_out[alto::kMaxModes] = {};    // values in that order

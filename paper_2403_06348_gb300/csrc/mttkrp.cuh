@@ -48,6 +48,12 @@ struct MttkrpArgs {
   const int *skip;             // nonzero: return at once (inner loop converged)
   // output-oriented traversal (Alg. 4): pos_out of the output mode [nnz]
   const uint32_t *perm;
+  // in-tile output-oriented traversal (TILED): htab holds nbins hot rows, the
+  // first nslots of them staged in shared memory, the rest ("warm") summed in
+  // kWarmReps replicas [kWarmReps][nbins][R] (zero between launches)
+  int nbins;
+  float *warm;
+  uint32_t *status;            // device status word (kStatusTimeout)
 };
 
 // Shared memory the segment kernel needs.
@@ -98,5 +104,26 @@ cudaError_t launch_phi_out_nt(const MttkrpArgs &a, bool pre, size_t smem, int nu
 template <int NT>
 cudaError_t launch_phi_nt(const MttkrpArgs &a, bool pull, bool pre, size_t smem, int num_sms,
                           cudaStream_t s);
+
+// MTTKRP over the one ALTO copy, output-oriented inside each tile (tile.cuh):
+// a.htab / a.nbins / a.nslots / a.slot_rows the mode's hot rows, a.warm the
+// replicas when nbins > nslots (then followed by launch_warm_reduce).
+cudaError_t launch_mttkrp_tile(const MttkrpArgs &a, int cpl, bool bf16, bool group, int num_sms,
+                               cudaStream_t s);
+
+template <int NT>
+cudaError_t launch_mttkrp_tile_nt(const MttkrpArgs &a, int cpl, bool bf16, bool group, int num_sms,
+                                  cudaStream_t s);
+
+// Shared memory of one TILED CTA for nmodes, key width kw, rank R, cpl.
+size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits, int nbins);
+
+// out(row of warm slot i, :) = sum of the kWarmReps replicas of slot i, for
+// slots nslots..nbins-1; the replicas are zeroed again for the next launch.
+cudaError_t launch_warm_reduce(float *warm, const uint32_t *slot_rows, int nslots, int nbins, int R,
+                               float *out, int num_sms, cudaStream_t s);
+
+// Replicas of the warm rows used by the TILED kernel.
+constexpr int kTileWarmReps = 16;
 
 }  // namespace alto

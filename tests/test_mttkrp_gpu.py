@@ -156,7 +156,7 @@ def test_bad_arguments_rejected():
 # the fp64 oracle computed row by row
 # ---------------------------------------------------------------------------
 
-def _full_size_rows(spec, R, bf16=False, nrand=192, nhot=64, seed=10):
+def _full_size_rows(spec, R, bf16=False, nrand=192, nhot=64, seed=10, variant=0):
     import torch
     coords, vals = synth.cached(spec)
     coords = np.asarray(coords)
@@ -166,6 +166,7 @@ def _full_size_rows(spec, R, bf16=False, nrand=192, nhot=64, seed=10):
     Ad = gu.gpu_factors(A, torch.bfloat16 if bf16 else torch.float32)
     rng = np.random.default_rng(seed)
     for n in range(len(spec.dims)):
+        t.set_mode_plan(n, variant)
         got = t.mttkrp(n, Ad, R)
         counts = np.bincount(coords[n], minlength=spec.dims[n])
         hot = np.argsort(-counts, kind="stable")[:nhot]
@@ -182,16 +183,19 @@ def _full_size_rows(spec, R, bf16=False, nrand=192, nhot=64, seed=10):
 
 
 @pytest.mark.slow
-def test_full_size_zipf3d():
-    _full_size_rows(synth.ZIPF3D, 32)
+@pytest.mark.parametrize("variant", [0, 4])
+def test_full_size_zipf3d(variant):
+    _full_size_rows(synth.ZIPF3D, 32, variant=variant)
 
 
 @pytest.mark.slow
-def test_full_size_count4d():
-    _full_size_rows(synth.COUNT4D, 16)
+@pytest.mark.parametrize("variant", [0, 4])
+def test_full_size_count4d(variant):
+    _full_size_rows(synth.COUNT4D, 16, variant=variant)
 
 
 @pytest.mark.slow
-def test_full_size_zipf5d_fp32_and_bf16():
-    _full_size_rows(synth.ZIPF5D, 64)
-    _full_size_rows(synth.ZIPF5D, 64, bf16=True)
+@pytest.mark.parametrize("variant", [0, 4])
+def test_full_size_zipf5d_fp32_and_bf16(variant):
+    _full_size_rows(synth.ZIPF5D, 64, variant=variant)
+    _full_size_rows(synth.ZIPF5D, 64, bf16=True, variant=variant)
