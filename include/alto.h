@@ -141,7 +141,9 @@ typedef struct alto_mode_plan {
   int hot_rows;       /* ATOMIC: staged hot rows, -1 = as many as fit; OUTPUT:
                          resolved to the hot rows its long runs may stage
                          (set by the library, up to 256); TILED, TILED_LINE:
-                         resolved to the hot rows staged in shared memory      */
+                         at most this many hot rows staged in shared memory
+                         (-1 = as many as fit two CTAs per SM), resolved to
+                         the number staged                                      */
 } alto_mode_plan;
 
 /* ---------------------------------------------------------------------------

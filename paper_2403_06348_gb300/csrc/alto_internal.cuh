@@ -209,6 +209,35 @@ __device__ __forceinline__ void decode_all(const DecodePlan &dp, uint64_t lo, ui
 }
 
 // ---------------------------------------------------------------------------
+// Byte-table de-linearization (EXTRACT of Alg. 3) for positions of at most 64
+// bits. The position's bits are a fixed permutation of the coordinates' bits,
+// so every byte of the position contributes disjoint bits: table[b][v] holds
+// the bits that byte value v at byte b contributes, with the coordinates
+// packed by rank (rank q at bit off[q], bits[q] wide). A position's packed
+// coordinates are the OR of its eight bytes' entries.
+// ---------------------------------------------------------------------------
+constexpr int kLutEntries = 8 * 256;
+constexpr size_t kLutBytes = (size_t)kLutEntries * sizeof(uint64_t);
+
+struct LutPlan {
+  uint8_t off[kMaxModes];   // bit of rank q in the packed word
+  uint8_t bits[kMaxModes];  // its width
+};
+
+template <int NMAX>
+__device__ __forceinline__ void decode_lut(const uint64_t *__restrict__ T, const LutPlan &lp, uint64_t key,
+                                           uint32_t (&c)[NMAX]) {
+  const uint32_t l = (uint32_t)key, h = (uint32_t)(key >> 32);
+  const uint64_t p = (T[l & 255u] | T[256 + ((l >> 8) & 255u)] | T[512 + ((l >> 16) & 255u)] |
+                      T[768 + (l >> 24)]) |
+                     (T[1024 + (h & 255u)] | T[1280 + ((h >> 8) & 255u)] | T[1536 + ((h >> 16) & 255u)] |
+                      T[1792 + (h >> 24)]);
+#pragma unroll
+  for (int q = 0; q < NMAX; ++q)
+    c[q] = (uint32_t)(p >> lp.off[q]) & (uint32_t)((1ull << lp.bits[q]) - 1ull);
+}
+
+// ---------------------------------------------------------------------------
 // Raw vector memory helpers (inline PTX)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void red_add_v4(float *addr, float a, float b, float c, float d) {

@@ -372,6 +372,42 @@ alto_status build_hot_table(alto_tensor *h, int n, int nslots, HotTable &ht, cud
   return ALTO_OK;
 }
 
+// The byte table of the one-word decode (positions of at most 64 bits),
+// built on the host from the bit plan on first use and kept in the handle.
+alto_status ensure_lut(alto_tensor *h, cudaStream_t s) {
+  if (h->kw != 1 || h->lut_dev) return ALTO_OK;
+  LutPlan lp{};
+  int off = 0;
+  for (int q = 0; q < h->N; ++q) {
+    const int b = h->bits[h->mode_of[q]];
+    lp.off[q] = (uint8_t)(b ? off : 0);
+    lp.bits[q] = (uint8_t)b;
+    off += b;
+  }
+  std::vector<uint64_t> tab(kLutEntries, 0);
+  for (int b = 0; b < 8; ++b)
+    for (int v = 0; v < 256; ++v) {
+      const uint64_t key = (uint64_t)v << (8 * b);
+      uint64_t packed = 0;
+      for (int n = 0; n < h->N; ++n) {
+        uint64_t c = 0;
+        int k = 0;
+        for (int i = 0; i < 64; ++i)
+          if ((h->mask_lo[n] >> i) & 1ull) c |= ((key >> i) & 1ull) << k++;
+        packed |= c << lp.off[h->rank_of[n]];
+      }
+      tab[b * 256 + v] = packed;
+    }
+  uint64_t *d = nullptr;
+  alto_status st = alloc_n(h, &d, kLutEntries, s, "decode table");
+  if (st != ALTO_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(d, tab.data(), kLutBytes, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  h->lut_dev = d;
+  h->lut_plan = lp;
+  return ALTO_OK;
+}
+
 alto_status ensure_hot_table(alto_tensor *h, int n, int nslots, cudaStream_t s) {
   return build_hot_table(h, n, nslots, h->hot_tab[n], s);
 }
@@ -441,6 +477,13 @@ int hbits_for(int k) {
 
 int tile_bins(const alto_tensor *h, int mode) { return std::min<int>((int)h->nhot[mode], kTileBins); }
 
+// The byte-table decode is used when positions take one word and the table
+// fits beside the rest of the layout.
+bool tile_lut(const alto_tensor *h, int mode, int R, int cpl) {
+  const int nb = tile_bins(h, mode);
+  return h->kw == 1 && tile_smem_bytes(h->N, h->kw, R, cpl, 0, hbits_for(nb), nb, true) <= mttkrp_smem_limit();
+}
+
 int tile_slots(const alto_tensor *h, int mode, int R, int cpl) {
   const int nb = tile_bins(h, mode);
   const int hb = hbits_for(nb);
@@ -450,7 +493,7 @@ int tile_slots(const alto_tensor *h, int mode, int R, int cpl) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   }
-  const size_t base = tile_smem_bytes(h->N, h->kw, R, cpl, 0, hb, nb);
+  const size_t base = tile_smem_bytes(h->N, h->kw, R, cpl, 0, hb, nb, tile_lut(h, mode, R, cpl));
   size_t target = (size_t)per_sm / 2 - 1024;  // two CTAs per SM
   if (target > mttkrp_smem_limit()) target = mttkrp_smem_limit();
   if (base >= target) return 0;
@@ -460,13 +503,25 @@ int tile_slots(const alto_tensor *h, int mode, int R, int cpl) {
 
 bool tile_variant(int v) { return v == ALTO_VARIANT_TILED || v == ALTO_VARIANT_TILED_LINE; }
 
+// Whether a TILED CTA (no staged rows) fits the shared memory of one block.
+bool tile_fits(const alto_tensor *h, int mode, int R, int cpl) {
+  const int nb = tile_bins(h, mode);
+  return tile_smem_bytes(h->N, h->kw, R, cpl, 0, hbits_for(nb), nb, false) <= mttkrp_smem_limit();
+}
+
 alto_status resolve_plan(alto_tensor *h, int mode, int R, alto_mode_plan *out) {
   alto_mode_plan p = h->plan[mode];
   if (tile_variant(p.variant) && h->dims[mode] > 0x80000000ull) p.variant = ALTO_VARIANT_ATOMIC;
   if (tile_variant(p.variant)) {
     const bool wide = R >= 8 && (p.cols_per_lane == 0 || p.cols_per_lane >= 8);
     p.cols_per_lane = wide ? 8 : 4;
-    p.hot_rows = tile_slots(h, mode, R, p.cols_per_lane);
+    // more lanes per nonzero means fewer groups and fewer skew slots
+    if (!tile_fits(h, mode, R, p.cols_per_lane) && R >= 8) p.cols_per_lane = 8;
+    if (!tile_fits(h, mode, R, p.cols_per_lane)) p.variant = ALTO_VARIANT_ATOMIC;
+  }
+  if (tile_variant(p.variant)) {
+    const int fit = tile_slots(h, mode, R, p.cols_per_lane);
+    p.hot_rows = p.hot_rows >= 0 ? std::min(p.hot_rows, fit) : fit;
     *out = p;
     return ALTO_OK;
   }
@@ -624,6 +679,12 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     a.vals = h->vals_out[mode];
     size_t smem = 0;
     if ((st = out_staging(h, mode, R, a, &smem, s)) != ALTO_OK) return st;
+    if (h->kw == 1 && smem + kLutBytes <= mttkrp_stage_budget()) {
+      if ((st = ensure_lut(h, s)) != ALTO_OK) return st;
+      a.lut = h->lut_dev;
+      a.lp = h->lut_plan;
+      smem += kLutBytes;
+    }
     {
       ProfScope ps(h, ALTO_PROF_ZERO, s);
       CUDA_TRY(cudaMemsetAsync(out, 0, I * R * sizeof(float), s));
@@ -636,8 +697,19 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     if (p.cols_per_lane == 8 && !bf16)
       for (int m = 0; m < h->N; ++m)
         if (m != mode && ((uintptr_t)factors[m] & 31u) != 0) p.cols_per_lane = 4;
+    if (!tile_fits(h, mode, R, p.cols_per_lane)) {
+      // 16-byte aligned factors force 4 columns per lane, whose layout does
+      // not fit here: run the mode as ATOMIC instead
+      const alto_mode_plan saved = h->plan[mode];
+      h->plan[mode] = alto_mode_plan{ALTO_VARIANT_ATOMIC, 4, -1};
+      st = resolve_plan(h, mode, R, &p);
+      h->plan[mode] = saved;
+      if (st != ALTO_OK) return st;
+    }
+  }
+  if (tile_variant(p.variant)) {
     const int nb = tile_bins(h, mode);
-    const int nslots = std::min(tile_slots(h, mode, R, p.cols_per_lane), nb);
+    const int nslots = std::min({p.hot_rows, tile_slots(h, mode, R, p.cols_per_lane), nb});
     const HotTable *tab = nullptr;
     if ((st = ensure_group_hot(h, mode, nb, s, &tab)) != ALTO_OK) return st;
     a.htab = tab->htab;
@@ -646,6 +718,11 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
     a.nslots = std::min(nslots, a.nbins);
     a.slot_rows = h->hot_rows[mode];
     a.status = h->status_dev;
+    if (tile_lut(h, mode, R, p.cols_per_lane)) {
+      if ((st = ensure_lut(h, s)) != ALTO_OK) return st;
+      a.lut = h->lut_dev;
+      a.lp = h->lut_plan;
+    }
     if (a.nbins > a.nslots) {
       const size_t need = (size_t)kTileWarmReps * (size_t)a.nbins * (size_t)R * sizeof(float);
       if (h->warm.bytes < need) {
@@ -1066,6 +1143,7 @@ void alto_free(alto_handle_t h) {
   dfree(h, h->norm_sq_dev, 8, s);
   dfree(h, h->nhot_dev, kMaxModes * 4, s);
   dfree(h, h->dp_rank_dev, sizeof(DecodePlan32), s);
+  dfree(h, h->lut_dev, kLutBytes, s);
   delete h;
 }
 
@@ -1513,7 +1591,7 @@ alto_status alto_autotune(alto_handle_t h, int R, const void *const *factors, al
       if (L == L0 && h->dims[n] <= 0x80000000ull)
         for (int v : {ALTO_VARIANT_TILED, ALTO_VARIANT_TILED_LINE})
           for (int c : cpls)
-            if (R % c == 0 && (c == 4 || R >= 8)) cands.push_back(alto_mode_plan{v, c, 0});
+            if (R % c == 0 && (c == 4 || R >= 8)) cands.push_back(alto_mode_plan{v, c, -1});
       if (cands.empty()) cands.push_back(alto_mode_plan{ALTO_VARIANT_AUTO, 0, -1});
       double bms = 1e300;
       alto_mode_plan bp{};

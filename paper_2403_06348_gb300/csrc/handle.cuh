@@ -123,6 +123,8 @@ struct alto_tensor {
   uint32_t *status_dev = nullptr;
   double *norm_sq_dev = nullptr;
   DecodePlan32 *dp_rank_dev = nullptr;   // runs by rank, for grouped launches
+  uint64_t *lut_dev = nullptr;            // byte-table decode [8][256] (positions <= 64 bits)
+  alto::LutPlan lut_plan{};               // its packing, by rank
   uint32_t *hot_rows[alto::kMaxModes] = {};
   uint32_t *nhot_dev = nullptr;
   // host mirrors

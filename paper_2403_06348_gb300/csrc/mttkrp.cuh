@@ -54,6 +54,10 @@ struct MttkrpArgs {
   int nbins;
   float *warm;
   uint32_t *status;            // device status word (kStatusTimeout)
+  // byte-table decode (one-word positions): the table [8][256] in global
+  // memory, copied into shared memory by the kernels that use it; null: none
+  const uint64_t *lut;
+  LutPlan lp;
 };
 
 // Shared memory the segment kernel needs.
@@ -116,7 +120,7 @@ cudaError_t launch_mttkrp_tile_nt(const MttkrpArgs &a, int cpl, bool bf16, bool 
                                   cudaStream_t s);
 
 // Shared memory of one TILED CTA for nmodes, key width kw, rank R, cpl.
-size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits, int nbins);
+size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits, int nbins, bool lut);
 
 // out(row of warm slot i, :) = sum of the kWarmReps replicas of slot i, for
 // slots nslots..nbins-1; the replicas are zeroed again for the next launch.

@@ -83,6 +83,13 @@ __global__ void __launch_bounds__(kMttkrpThreads,
   float *temp = reinterpret_cast<float *>(sm);
   uint64_t *htab = reinterpret_cast<uint64_t *>(temp + (size_t)a.nslots * R);
   const bool staged = a.nslots > 0;
+  // the byte table of the one-word decode follows the hot-row table
+  const bool use_lut = KW == 1 && a.lut != nullptr;
+  uint64_t *lut = htab + ((size_t)1 << a.hbits);
+  if (use_lut) {
+    for (int i = threadIdx.x; i < kLutEntries; i += blockDim.x) lut[i] = a.lut[i];
+    if (!staged) __syncthreads();
+  }
   if (staged) {
     const int hsize = 1 << a.hbits;
     for (int i = threadIdx.x; i < hsize; i += blockDim.x) htab[i] = a.htab[i];
@@ -134,7 +141,9 @@ __global__ void __launch_bounds__(kMttkrpThreads,
       // the next batch's nonzero is loaded while this one runs
       load_nz(b + 1);
       uint32_t c[NMAX];
-      if constexpr (NT > 0)
+      if (use_lut)
+        decode_lut<NMAX>(lut, a.lp, lo, c);
+      else if constexpr (NT > 0)
         decode_blocks<KW, NMAX, 0>(a.bp, lo, hi, c);
       else
         decode_runs<KW, NMAX>(a.dp, N, lo, hi, c);

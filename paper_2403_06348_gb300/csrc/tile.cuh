@@ -35,7 +35,7 @@ namespace alto {
 
 constexpr int kTileThreads = 512;
 #ifndef ALTO_TILE_NPT
-#define ALTO_TILE_NPT 2
+#define ALTO_TILE_NPT 4
 #endif
 constexpr int kTileNpt = ALTO_TILE_NPT;                 // nonzeros decoded per thread
 constexpr int kTileNnz = kTileThreads * kTileNpt;      // nonzeros per tile
@@ -58,23 +58,24 @@ struct TileLayout {
   uint32_t htab;   // hot-row hash table [2^hbits] (slot << 32 | row)
   uint32_t bins;   // bin counts / offsets [nbins + 1] and 32 scan words
   uint32_t bar;    // two mbarriers
+  uint32_t lut;    // byte-table decode [8][256] (one-word positions), if used
   uint32_t total;
 };
 
-// piece = records one group walks per tile (kTileNpt * R / CPL); the records
-// of piece g are skewed by g slots so that the groups of a warp, reading
-// their pieces' j-th records together, hit different banks.
-__host__ __device__ inline TileLayout tile_layout(int kw, int rec_bytes, int piece, int R, int nslots,
-                                                  int hbits, int nbins) {
+// ngroups = groups of R / CPL lanes per CTA: the record slots hold the tile
+// plus one skew slot per group (and one spare).
+__host__ __device__ inline TileLayout tile_layout(int kw, int rec_bytes, int ngroups, int R, int nslots,
+                                                  int hbits, int nbins, bool lut) {
   TileLayout L{};
   const uint32_t raw = (uint32_t)kTileNnz * (8u * kw + 4u);
-  const uint32_t rec = ((uint32_t)kTileNnz + (uint32_t)kTileNnz / (uint32_t)piece + 1u) * (uint32_t)rec_bytes;
+  const uint32_t rec = ((uint32_t)kTileNnz + (uint32_t)ngroups + 1u) * (uint32_t)rec_bytes;
   L.buf = tile_round(raw > rec ? raw : rec, 128);
   L.stage = 2 * L.buf;
   L.htab = L.stage + tile_round((uint32_t)nslots * (uint32_t)R * 4u, 16);
   L.bins = L.htab + (1u << hbits) * 8u;
   L.bar = tile_round(L.bins + ((uint32_t)nbins + 1u + 32u) * 4u, 16);
-  L.total = L.bar + 16;
+  L.lut = L.bar + 16;
+  L.total = L.lut + (lut ? (uint32_t)kLutBytes : 0u);
   return L;
 }
 
@@ -230,6 +231,111 @@ __device__ __forceinline__ void tile_flush(const uint64_t (&run)[CPL / 2], uint3
     red_v4(o + CPL * sub + 4 * v, f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
 }
 
+// Gathers this lane's columns of the N-1 input rows of record w.
+template <int NT, int CPL, bool BF16, int NIN>
+__device__ __forceinline__ void tile_gather(const uint32_t *w, const char *const (&fb)[NIN], uint32_t rowb,
+                                            uint64_t (&g)[NIN][CPL / 2]) {
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) load_row_f2<CPL, BF16>(fb[q] + (uint64_t)w[1 + q] * rowb, g[q]);
+}
+
+// Reads the RW words of a record.
+template <int RW>
+__device__ __forceinline__ void tile_rec(const uint32_t *rp, uint32_t (&w)[RW]) {
+#pragma unroll
+  for (int q = 0; q < RW / 4; ++q) {
+    const uint4 u = reinterpret_cast<const uint4 *>(rp)[q];
+    w[4 * q] = u.x;
+    w[4 * q + 1] = u.y;
+    w[4 * q + 2] = u.z;
+    w[4 * q + 3] = u.w;
+  }
+}
+
+// Walks n records starting at rp, stride `step` records. MERGE: runs of
+// equal row code are summed in registers and leave when the code changes;
+// otherwise every record leaves on its own (rows without a hot code go
+// straight to the output).
+template <int NT, int CPL, bool BF16, int RW, bool MERGE, int NIN>
+__device__ __forceinline__ void tile_walk(const uint32_t *rp, int step, int n, const char *const (&fb)[NIN],
+                                          uint32_t rowb, int N, const MttkrpArgs &a, float *stage, int sub,
+                                          int tpn, int grp) {
+  uint64_t run[CPL / 2];
+#pragma unroll
+  for (int c = 0; c < CPL / 2; ++c) run[c] = 0ull;
+  uint32_t run_code = kEmptyRow;
+  if constexpr (NT > 0) {
+#pragma unroll 2
+    for (int i = 0; i < n; ++i) {
+      uint32_t w[RW];
+      tile_rec<RW>(rp + (size_t)i * step * RW, w);
+      uint64_t g[NIN][CPL / 2];
+      tile_gather<NT, CPL, BF16, NIN>(w, fb, rowb, g);
+      // t = v * A_0 ... A_{N-3}; contribution = t * A_{N-2}
+      uint64_t tv[CPL / 2];
+      const uint64_t vv = f2_splat(__uint_as_float(w[RW - 1]));
+#pragma unroll
+      for (int c = 0; c < CPL / 2; ++c) tv[c] = vv;
+#pragma unroll
+      for (int q = 0; q + 1 < NIN; ++q)
+#pragma unroll
+        for (int c = 0; c < CPL / 2; ++c) tv[c] = f2_mul(tv[c], g[q][c]);
+      if constexpr (MERGE) {
+        if (w[0] != run_code) {
+          if (run_code != kEmptyRow) tile_flush<CPL>(run, run_code, a, stage, sub, tpn, grp);
+#pragma unroll
+          for (int c = 0; c < CPL / 2; ++c) run[c] = 0ull;
+          run_code = w[0];
+        }
+#pragma unroll
+        for (int c = 0; c < CPL / 2; ++c) run[c] = f2_fma(tv[c], g[NIN - 1][c], run[c]);
+      } else {
+        uint64_t pr[CPL / 2];
+#pragma unroll
+        for (int c = 0; c < CPL / 2; ++c) pr[c] = f2_mul(tv[c], g[NIN - 1][c]);
+        float *o = a.out + (uint64_t)w[0] * (uint64_t)a.R + CPL * sub;
+#pragma unroll
+        for (int v = 0; v < CPL / 4; ++v)
+          red_v4(o + 4 * v, f2_lo(pr[2 * v]), f2_hi(pr[2 * v]), f2_lo(pr[2 * v + 1]), f2_hi(pr[2 * v + 1]));
+      }
+    }
+  } else {
+    for (int i = 0; i < n; ++i) {
+      uint32_t w[RW];
+      tile_rec<RW>(rp + (size_t)i * step * RW, w);
+      uint64_t tv[CPL / 2];
+      const uint64_t vv = f2_splat(__uint_as_float(w[RW - 1]));
+#pragma unroll
+      for (int c = 0; c < CPL / 2; ++c) tv[c] = vv;
+#pragma unroll
+      for (int q = 0; q < NIN; ++q) {
+        if (q + 1 < N) {
+          uint64_t f[CPL / 2];
+          load_row_f2<CPL, BF16>(fb[q] + (uint64_t)w[1 + q] * rowb, f);
+#pragma unroll
+          for (int c = 0; c < CPL / 2; ++c) tv[c] = f2_mul(tv[c], f[c]);
+        }
+      }
+      if (MERGE) {
+        if (w[0] != run_code) {
+          if (run_code != kEmptyRow) tile_flush<CPL>(run, run_code, a, stage, sub, tpn, grp);
+#pragma unroll
+          for (int c = 0; c < CPL / 2; ++c) run[c] = 0ull;
+          run_code = w[0];
+        }
+#pragma unroll
+        for (int c = 0; c < CPL / 2; ++c) run[c] = f2_add(run[c], tv[c]);
+      } else {
+        float *o = a.out + (uint64_t)w[0] * (uint64_t)a.R + CPL * sub;
+#pragma unroll
+        for (int v = 0; v < CPL / 4; ++v)
+          red_v4(o + 4 * v, f2_lo(tv[2 * v]), f2_hi(tv[2 * v]), f2_lo(tv[2 * v + 1]), f2_hi(tv[2 * v + 1]));
+      }
+    }
+  }
+  if (MERGE && run_code != kEmptyRow) tile_flush<CPL>(run, run_code, a, stage, sub, tpn, grp);
+}
+
 // ---------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------
@@ -243,10 +349,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
   const int tpn = R / CPL;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = lane / tpn, sub = lane - grp * tpn;
-  const int piece = kTileNpt * tpn;
   const int ro = a.out_rank;
   const unsigned full = 0xffffffffu;
-  const TileLayout lay = tile_layout(KW, RW * 4, piece, R, a.nslots, a.hbits, a.nbins);
+  const bool use_lut = KW == 1 && a.lut != nullptr;
+  const TileLayout lay = tile_layout(KW, RW * 4, kTileThreads / tpn, R, a.nslots, a.hbits, a.nbins, use_lut);
 
   extern __shared__ __align__(16) unsigned char sm[];
   float *stage = reinterpret_cast<float *>(sm + lay.stage);
@@ -254,6 +360,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
   uint32_t *bins = reinterpret_cast<uint32_t *>(sm + lay.bins);
   uint32_t *scan_w = bins + a.nbins + 1;
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + lay.bar);
+  uint64_t *lut = reinterpret_cast<uint64_t *>(sm + lay.lut);
+  if (use_lut)
+    for (int i = tid; i < kLutEntries; i += kTileThreads) lut[i] = a.lut[i];
 
   const int hsize = 1 << a.hbits;
   for (int i = tid; i < hsize; i += kTileThreads) htab[i] = a.htab[i];
@@ -346,7 +455,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
         }
       }
       uint32_t c[NMAX];
-      if constexpr (NT > 0)
+      if (use_lut)
+        decode_lut<NMAX>(lut, a.lp, lo, c);
+      else if constexpr (NT > 0)
         decode_blocks<KW, NMAX, 0>(a.bp, lo, hi, c);
       else
         decode_runs<KW, NMAX>(a.dp, N, lo, hi, c);
@@ -363,6 +474,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
     }
 
     uint32_t pos[kTileNpt];
+    uint32_t bins_hot_count = 0;
     if constexpr (GROUP) {
       // ---- counting sort by bin: hot row idx -> bin idx, others -> nbins --
       uint32_t rank[kTileNpt], bin[kTileNpt];
@@ -407,6 +519,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
         run_off += c0;
       }
       __syncthreads();
+      bins_hot_count = bins[a.nbins];  // records of hot rows (they sort first)
 #pragma unroll
       for (int k = 0; k < kTileNpt; ++k) {
         const int x = tid + k * kTileThreads;
@@ -417,13 +530,24 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
 #pragma unroll
       for (int k = 0; k < kTileNpt; ++k) pos[k] = (uint32_t)(tid + k * kTileThreads);
     }
-    // ---- records into the tile buffer (piece g skewed by g slots) -------
+    // ---- records into the tile buffer -----------------------------------
+    // Sorted order (GROUP): hot bins [0, nhot) first, then the other rows;
+    // in line order (no GROUP) the whole tile is the merged part. Group g
+    // walks the contiguous piece [g * hpiece, (g + 1) * hpiece) of the hot part
+    // (runs merged; piece g skewed by g slots so that the groups of a warp
+    // read different banks) and the records nhot + g, nhot + g + G, ... of
+    // the rest (one update each; consecutive groups read consecutive slots).
+    const int ngroups = kTileThreads / tpn;
+    const int nhot = GROUP ? (int)bins_hot_count : cnt;  // line order: one merged part
+    const int hpiece = (nhot + ngroups - 1) / ngroups;
+    const int cold_base = nhot + (hpiece ? (nhot + hpiece - 1) / hpiece : 0);
     uint32_t *rec = reinterpret_cast<uint32_t *>(buf);
 #pragma unroll
     for (int k = 0; k < kTileNpt; ++k) {
       const int x = tid + k * kTileThreads;
       if (x < cnt) {
-        const uint32_t ph = pos[k] + pos[k] / (uint32_t)piece;
+        const int pk = (int)pos[k];
+        const int phys = pk < nhot ? pk + pk / hpiece : cold_base + (pk - nhot);
         uint32_t w[RW];
         w[0] = code[k];
 #pragma unroll
@@ -431,7 +555,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
 #pragma unroll
         for (int q = NIN + 1; q < RW - 1; ++q) w[q] = 0u;
         w[RW - 1] = __float_as_uint(val[k]);
-        uint4 *dst = reinterpret_cast<uint4 *>(rec + (size_t)ph * RW);
+        uint4 *dst = reinterpret_cast<uint4 *>(rec + (size_t)phys * RW);
 #pragma unroll
         for (int q = 0; q < RW / 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       }
@@ -443,69 +567,20 @@ __global__ void __launch_bounds__(kTileThreads, 2) mttkrp_tile_kernel(const __gr
 
     // ---- gather, multiply, merge runs (Alg. 4 output-oriented updates) --
     const int gw = warp * (32 / tpn) + grp;
-    const int j0 = gw * piece;
-    const int j1 = (j0 + piece) < cnt ? (j0 + piece) : cnt;
-    uint64_t run[CPL / 2];
-#pragma unroll
-    for (int c = 0; c < CPL / 2; ++c) run[c] = 0ull;
-    uint32_t run_code = kEmptyRow;
-    const uint32_t *rp = rec + (size_t)(j0 + gw) * RW;  // skewed start of piece gw
-#pragma unroll 2
-    for (int j = j0; j < j1; ++j, rp += RW) {
-      uint32_t w[RW];
-#pragma unroll
-      for (int q = 0; q < RW / 4; ++q) {
-        const uint4 u = reinterpret_cast<const uint4 *>(rp)[q];
-        w[4 * q] = u.x;
-        w[4 * q + 1] = u.y;
-        w[4 * q + 2] = u.z;
-        w[4 * q + 3] = u.w;
-      }
-      const uint32_t cj = w[0];
-      uint64_t tv[CPL / 2];
-      const uint64_t vv = f2_splat(__uint_as_float(w[RW - 1]));
-#pragma unroll
-      for (int c = 0; c < CPL / 2; ++c) tv[c] = vv;
-      if constexpr (NT > 0) {
-        // t = v * A_0 ... A_{N-3}; run += t * A_{N-2}
-#pragma unroll
-        for (int q = 0; q + 1 < NIN; ++q) {
-          uint64_t f[CPL / 2];
-          load_row_f2<CPL, BF16>(fb[q] + (uint64_t)w[1 + q] * rowb, f);
-#pragma unroll
-          for (int c = 0; c < CPL / 2; ++c) tv[c] = f2_mul(tv[c], f[c]);
-        }
-        uint64_t f[CPL / 2];
-        load_row_f2<CPL, BF16>(fb[NIN - 1] + (uint64_t)w[NIN] * rowb, f);
-        if (cj != run_code) {
-          if (run_code != kEmptyRow) tile_flush<CPL>(run, run_code, a, stage, sub, tpn, grp);
-#pragma unroll
-          for (int c = 0; c < CPL / 2; ++c) run[c] = 0ull;
-          run_code = cj;
-        }
-#pragma unroll
-        for (int c = 0; c < CPL / 2; ++c) run[c] = f2_fma(tv[c], f[c], run[c]);
-      } else {
-#pragma unroll
-        for (int q = 0; q < NIN; ++q) {
-          if (q + 1 < N) {
-            uint64_t f[CPL / 2];
-            load_row_f2<CPL, BF16>(fb[q] + (uint64_t)w[1 + q] * rowb, f);
-#pragma unroll
-            for (int c = 0; c < CPL / 2; ++c) tv[c] = f2_mul(tv[c], f[c]);
-          }
-        }
-        if (cj != run_code) {
-          if (run_code != kEmptyRow) tile_flush<CPL>(run, run_code, a, stage, sub, tpn, grp);
-#pragma unroll
-          for (int c = 0; c < CPL / 2; ++c) run[c] = 0ull;
-          run_code = cj;
-        }
-#pragma unroll
-        for (int c = 0; c < CPL / 2; ++c) run[c] = f2_add(run[c], tv[c]);
-      }
+    if (nhot > 0) {
+      const int j0 = gw * hpiece;
+      const int j1 = (j0 + hpiece) < nhot ? (j0 + hpiece) : nhot;
+      if (j0 < j1)
+        tile_walk<NT, CPL, BF16, RW, true>(rec + (size_t)(j0 + gw) * RW, 1, j1 - j0, fb, rowb, N, a, stage,
+                                           sub, tpn, grp);
     }
-    if (run_code != kEmptyRow) tile_flush<CPL>(run, run_code, a, stage, sub, tpn, grp);
+    if (cnt > nhot) {
+      const int c0 = nhot + gw;
+      if (c0 < cnt)
+        tile_walk<NT, CPL, BF16, RW, false>(rec + (size_t)(cold_base + gw) * RW, ngroups,
+                                            (cnt - c0 + ngroups - 1) / ngroups, fb, rowb, N, a, stage, sub,
+                                            tpn, grp);
+    }
   }
 
   // the staged hot rows leave once per CTA
@@ -528,7 +603,8 @@ template <int NT, int KW, int CPL, bool BF16, bool GROUP>
 static cudaError_t launch_tile_one(const MttkrpArgs &a, int num_sms, cudaStream_t s) {
   auto kern = mttkrp_tile_kernel<NT, KW, CPL, BF16, GROUP>;
   constexpr int RW = tile_rec_words<NT ? NT : kMaxModes>();
-  const TileLayout lay = tile_layout(KW, RW * 4, kTileNpt * (a.R / CPL), a.R, a.nslots, a.hbits, a.nbins);
+  const TileLayout lay = tile_layout(KW, RW * 4, kTileThreads / (a.R / CPL), a.R, a.nslots, a.hbits, a.nbins,
+                                     KW == 1 && a.lut != nullptr);
   static int configured = 0;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

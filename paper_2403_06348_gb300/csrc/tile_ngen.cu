@@ -16,10 +16,10 @@ cudaError_t launch_mttkrp_tile(const MttkrpArgs &a, int cpl, bool bf16, bool gro
   }
 }
 
-size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits, int nbins) {
+size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits, int nbins, bool lut) {
   const int nmax = (nmodes == 3 || nmodes == 4 || nmodes == 5) ? nmodes : kMaxModes;
   const int rw = nmax + 1 <= 4 ? 4 : (nmax + 1 <= 8 ? 8 : 12);
-  return tile_layout(kw, rw * 4, kTileNpt * (R / cpl), R, nslots, hbits, nbins).total;
+  return tile_layout(kw, rw * 4, kTileThreads / (R / cpl), R, nslots, hbits, nbins, lut).total;
 }
 
 // One thread per 4 columns of a warm slot: the replicas summed in slot
