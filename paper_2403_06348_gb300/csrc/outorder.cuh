@@ -28,6 +28,10 @@ namespace alto {
 #define ALTO_OUT_MIN_BLOCKS 0  // 0: as the segment kernel (3 CTAs per SM, 2 for 8 columns)
 #endif
 constexpr int kOutUnroll = ALTO_OUT_UNROLL;
+#ifndef ALTO_OUT_PREFETCH
+#define ALTO_OUT_PREFETCH 1  // steps of the nonzero stream in flight per warp (deeper rings spill)
+#endif
+constexpr int kOutPrefetch = ALTO_OUT_PREFETCH;
 
 template <int CPL>
 constexpr int out_batches() {
@@ -105,28 +109,43 @@ __global__ void __launch_bounds__(kMttkrpThreads,
   const uint32_t nchunks = (nnz + chunk - 1) / chunk;
   const uint32_t piece = (uint32_t)tpn * kOutBatches;
 
+  // The warp's steps t = 0, 1, ... are (chunk warp_id + (t / B) nwarps,
+  // batch t % B); the entries of the next kOutPrefetch steps are in flight
+  // while a step is processed (a ring shifted by one each step).
+  auto step_pos = [&](uint32_t t, uint32_t &p) -> bool {
+    const uint32_t c = warp_id + (t / (uint32_t)kOutBatches) * nwarps;
+    p = c * chunk + (uint32_t)grp * piece + (uint32_t)sub + (t % (uint32_t)kOutBatches) * (uint32_t)tpn;
+    return c < nchunks && p < nnz;
+  };
+  uint64_t qlo[kOutPrefetch], qhi[kOutPrefetch];
+  float qv[kOutPrefetch];
+  uint32_t qx[kOutPrefetch];  // PRE: the nonzero's line position (its row of Pi)
+  auto load_step = [&](uint32_t t, int slot) {
+    uint32_t p;
+    qlo[slot] = 0;
+    qhi[slot] = 0;
+    qv[slot] = 0.f;
+    qx[slot] = 0;
+    if (step_pos(t, p)) {
+      if (KW == 1) {
+        qlo[slot] = __ldcs(reinterpret_cast<const unsigned long long *>(a.keys) + p);
+      } else {
+        const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2 *>(a.keys) + p);
+        qlo[slot] = kk.x;
+        qhi[slot] = kk.y;
+      }
+      qv[slot] = __ldcs(a.vals + p);
+      if (APR == kAprPre) qx[slot] = __ldcs(a.perm + p);
+    }
+  };
+  uint32_t t_next = 0;
+#pragma unroll
+  for (int d = 0; d < kOutPrefetch; ++d) load_step(t_next++, d);
+
   for (uint32_t ch = warp_id; ch < nchunks; ch += nwarps) {
-    // entry of the stored order this lane loads in batch b: p0 + b * tpn
+    // entry of the stored order this lane uses in batch b: p0 + b * tpn
     // (a.keys / a.vals hold the line positions and values in that order)
     const uint32_t p0 = ch * chunk + (uint32_t)grp * piece + (uint32_t)sub;
-    uint64_t nlo = 0, nhi = 0;
-    float nv = 0.f;
-    uint32_t nx = 0;  // PRE: the nonzero's line position (its row of Pi)
-    auto load_nz = [&](int b) {
-      const uint32_t p = p0 + (uint32_t)(b * tpn);
-      if (b < kOutBatches && p < nnz) {
-        if (KW == 1) {
-          nlo = __ldcs(reinterpret_cast<const unsigned long long *>(a.keys) + p);
-        } else {
-          const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2 *>(a.keys) + p);
-          nlo = kk.x;
-          nhi = kk.y;
-        }
-        nv = __ldcs(a.vals + p);
-        if (APR == kAprPre) nx = __ldcs(a.perm + p);
-      }
-    };
-    load_nz(0);
 
     float run[CPL];
 #pragma unroll
@@ -135,11 +154,17 @@ __global__ void __launch_bounds__(kMttkrpThreads,
     int run_n = 0;  // nonzeros in the run
     for (int b = 0; b < kOutBatches; ++b) {
       const bool valid = p0 + (uint32_t)(b * tpn) < nnz;
-      const uint64_t lo = nlo, hi = nhi;
-      const float v = nv;
-      const uint32_t xb = nx;
-      // the next batch's nonzero is loaded while this one runs
-      load_nz(b + 1);
+      const uint64_t lo = qlo[0], hi = qhi[0];
+      const float v = qv[0];
+      const uint32_t xb = qx[0];
+#pragma unroll
+      for (int d = 0; d + 1 < kOutPrefetch; ++d) {
+        qlo[d] = qlo[d + 1];
+        qhi[d] = qhi[d + 1];
+        qv[d] = qv[d + 1];
+        qx[d] = qx[d + 1];
+      }
+      load_step(t_next++, kOutPrefetch - 1);
       uint32_t c[NMAX];
       if (use_lut)
         decode_lut<NMAX>(lut, a.lp, lo, c);
@@ -155,7 +180,7 @@ __global__ void __launch_bounds__(kMttkrpThreads,
 #pragma unroll
       for (int k = 0; k < NIN; ++k) in[k] = (NMAX > 1 && k + 1 < NMAX) ? (k < ro ? c[k] : c[k + 1]) : 0u;
       const unsigned live = __ballot_sync(full, valid);
-      if (!live) break;
+      if (!live) continue;  // past the end (last chunk); the step ring stays in order
 #pragma unroll(CPL <= 8 ? kOutUnroll : 1)
       for (int q = 0; q < tpn; ++q) {
         const int j = grp * tpn + q;
