@@ -55,6 +55,10 @@ def parse_args():
                    help="library default plans instead of the autotuned ones")
     p.add_argument("--plans", default="",
                    help="per-mode plans 'variant:cols_per_lane,...' instead of tuning (profiling)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the per-mode MTTKRP measurements of the other workloads")
+    p.add_argument("--configs-scale", type=float, default=1.0,
+                   help="scale the nonzeros of the other workloads (testing only)")
     return p.parse_args()
 
 
@@ -202,6 +206,155 @@ def algorithmic_bytes_per_mode(coords, dims, R, key_bytes, fbytes=4):
         b += dims[n] * R * 4
         out.append(b)
     return out, D
+
+
+# ---------------------------------------------------------------------------
+# Per-mode MTTKRP measurements of every workload (configs 1-4)
+# ---------------------------------------------------------------------------
+
+VARIANT_NAMES = {0: "AUTO", 1: "ATOMIC", 2: "PULL", 3: "OUTPUT", 4: "TILED", 5: "TILED_LINE"}
+
+
+def time_modes(h, Ad, R, dims, reps=5):
+    """Per mode: average MTTKRP launch time (ms; the library's CUDA events on
+    the launching stream around the MTTKRP kernels, output zeroing excluded)
+    over ``reps`` calls after one warm-up call, and the resolved plan."""
+    import torch
+    out = torch.empty((max(dims), R), dtype=torch.float32, device="cuda")
+    res = []
+    for n in range(len(dims)):
+        o = out[:dims[n]]
+        h.mttkrp(n, Ad, R, out=o)
+        torch.cuda.synchronize()
+        h.profile_enable(True)
+        h.profile_read(reset=True)
+        for _ in range(reps):
+            h.mttkrp(n, Ad, R, out=o)
+        torch.cuda.synchronize()
+        launches, ms = h.profile_read(reset=True)["mttkrp"]
+        h.profile_enable(False)
+        res.append((ms / max(reps, 1), h.get_mode_plan(n, R)))
+    del out
+    return res
+
+
+def sampled_error(h, coords, vals, dims, A, Ad, R, nhot=64, nrand=64, seed=11):
+    """Max row-relative error of every mode's MTTKRP against the fp64 oracle
+    (oracle/coo_ref.c on the original fp32 factors) on sampled rows: the
+    nhot most frequent rows and nrand random rows of each mode."""
+    import torch
+    from oracle import alto_ref as ar
+    from oracle import cref
+    rng = np.random.default_rng(seed)
+    worst = []
+    for n in range(len(dims)):
+        got = h.mttkrp(n, Ad, R)
+        counts = np.bincount(coords[n], minlength=dims[n])
+        hot = np.argsort(-counts, kind="stable")[:nhot]
+        rnd = rng.choice(dims[n], size=min(nrand, dims[n]), replace=False)
+        rows = np.unique(np.concatenate([hot, rnd])).astype(np.uint32)
+        ref = cref.mttkrp_rows(coords, vals, dims, A, n, rows)
+        g = got[torch.from_numpy(rows.astype(np.int64)).cuda()].cpu().numpy()
+        err, bad = ar.row_relative_error(g, ref)
+        worst.append(float(err) if bad == 0 else float("inf"))
+        del got
+    return worst
+
+
+def config_entry(spec, coords, dims, R, kw, timed, fbytes, peak):
+    bytes_mode, _ = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw, fbytes)
+    M = coords.shape[1]
+    modes = []
+    for n, (ms, plan) in enumerate(timed):
+        gbs = bytes_mode[n] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        modes.append({"mode": n, "rows": int(dims[n]), "plan": VARIANT_NAMES.get(plan[0], plan[0]),
+                      "cols_per_lane": plan[1], "staged_rows": plan[2], "ms": ms,
+                      "nnz_r_per_s": M * R / (ms / 1e3) if ms > 0 else None,
+                      "algorithmic_bytes": bytes_mode[n], "gbs": gbs, "frac": gbs / peak})
+    tot_ms = sum(m["ms"] for m in modes)
+    return {"modes": modes, "all_modes_ms": tot_ms,
+            "nnz_r_per_s_all_modes": len(dims) * M * R / (tot_ms / 1e3) if tot_ms > 0 else None,
+            "mean_frac": sum(m["frac"] for m in modes) / len(modes)}
+
+
+def run_configs(args, alto, peak, headline=None):
+    """Per-mode MTTKRP of the four single-tensor workloads with autotuned plans
+    (configs 1, 3 and 4; config 4 with fp32 and with bf16 factors and its
+    error against the fp64 oracle), and the one-copy plans on the headline
+    tensor (TILED and ATOMIC: no stored order)."""
+    import torch
+    import synth
+    out = {"method": ("per mode: mean of 5 MTTKRP calls after one warm-up, CUDA events on the "
+                      "launching stream around the MTTKRP kernels (zeroing excluded); plans from "
+                      "alto_autotune unless named; frac = algorithmic bytes / time / peak")}
+
+    def load(spec):
+        if args.configs_scale != 1.0:
+            spec = synth.scaled(spec, max(1000, int(spec.nnz * args.configs_scale)))
+        c, v = synth.cached(spec)
+        return spec, np.asarray(c), np.asarray(v)
+
+    def tuned(spec, coords, vals, R, bf16=False, keep=False):
+        dims = spec.dims
+        h = alto.alto_encode(torch.from_numpy(coords.view(np.int32)).cuda(), torch.from_numpy(vals).cuda(),
+                             dims)
+        A = synth.factors(dims, R, seed=1)
+        Ad = [torch.from_numpy(a).cuda() for a in A]
+        if bf16:
+            Ad = [a.to(torch.bfloat16) for a in Ad]
+        h.autotune(Ad, R, segments=False, output=True)
+        timed = time_modes(h, Ad, R, dims)
+        kw = int(h.query().key_words)
+        return h, A, Ad, timed, kw
+
+    # config 1: 1000 x 800 x 600, 1e5 distinct uniform nonzeros, R = 16 (launch-bound)
+    spec, coords, vals = load(synth.UNIFORM3D)
+    h, A, Ad, timed, kw = tuned(spec, coords, vals, spec.rank)
+    e = config_entry(spec, coords, spec.dims, spec.rank, kw, timed, 4, peak)
+    e["workload"] = spec.name
+    e["bound"] = "launch latency (1.35 MB per mode)"
+    out["uniform3d_1e5"] = e
+    h.free()
+
+    # the headline tensor on the one-copy plans (no stored order)
+    if headline is not None:
+        spec, coords, vals = headline
+        h = alto.alto_encode(torch.from_numpy(coords.view(np.int32)).cuda(), torch.from_numpy(vals).cuda(),
+                             spec.dims)
+        Ad = [torch.from_numpy(a).cuda() for a in synth.factors(spec.dims, spec.rank, seed=1)]
+        kw = int(h.query().key_words)
+        one_copy = {}
+        for variant, cpl in ((4, 8), (4, 4), (1, 4)):
+            for n in range(len(spec.dims)):
+                h.set_mode_plan(n, variant, cpl)
+            timed = time_modes(h, Ad, spec.rank, spec.dims)
+            one_copy[f"{VARIANT_NAMES[variant]}:{cpl}"] = config_entry(spec, coords, spec.dims, spec.rank,
+                                                                       kw, timed, 4, peak)
+        best = min(one_copy, key=lambda k: one_copy[k]["all_modes_ms"])
+        out["zipf3d_1e8_one_copy"] = {"workload": spec.name, "plans": one_copy, "best": best}
+        h.free()
+
+    # config 3: 4-mode count tensor, 2e8 nonzeros, R = 16, every mode autotuned
+    spec, coords, vals = load(synth.COUNT4D)
+    h, A, Ad, timed, kw = tuned(spec, coords, vals, spec.rank)
+    e = config_entry(spec, coords, spec.dims, spec.rank, kw, timed, 4, peak)
+    e["workload"] = spec.name
+    out["count4d_2e8"] = e
+    h.free()
+    del coords, vals
+
+    # config 4: 5-mode Zipf tensor, 1.5e8 nonzeros, 128-bit positions, R = 64,
+    # fp32 and bf16 factors, error against the fp64 oracle on sampled rows
+    spec, coords, vals = load(synth.ZIPF5D)
+    for bf16 in (False, True):
+        h, A, Ad, timed, kw = tuned(spec, coords, vals, spec.rank, bf16=bf16)
+        e = config_entry(spec, coords, spec.dims, spec.rank, kw, timed, 2 if bf16 else 4, peak)
+        e["workload"] = spec.name + (" bf16 factors" if bf16 else " fp32 factors")
+        e["max_row_rel_err_vs_fp64_oracle"] = sampled_error(h, coords, vals, spec.dims, A, Ad, spec.rank)
+        e["error_sample"] = "64 most frequent + 64 random rows per mode"
+        out["zipf5d_1.5e8_" + ("bf16" if bf16 else "fp32")] = e
+        h.free()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -398,6 +551,8 @@ def run_ours(args):
 
     if not args.no_e2e:
         line["e2e"] = run_e2e(args, alto, coords, vals, spec, A0, world, barrier, plans)
+    if not args.no_configs and world == 1:
+        line["configs"] = run_configs(args, alto, peak, headline=(spec, coords, vals))
     if not args.no_serve:
         line["serving"] = run_serving(args, alto)
     if not args.no_cpapr and world == 1:

@@ -28,6 +28,8 @@ struct CpArgs {
 
 cudaError_t launch_gram(const float *A, uint64_t I, int R, double *G, int num_sms, cudaStream_t s);
 cudaError_t launch_prepare(const CpArgs &a, cudaStream_t s);
+// B = M W into B with BtB += B^T B and dot += diag(M^T B) (both zeroed by
+// the caller); one pass over M.
 cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, int R, double *BtB,
                           double *dot, const int *done_at, int it, int num_sms, cudaStream_t s);
 cudaError_t launch_finish(const CpArgs &a, cudaStream_t s);
