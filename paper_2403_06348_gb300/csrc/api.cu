@@ -1382,6 +1382,7 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
   const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_s = take((size_t)N * R * 8),
                o_Sn = take((size_t)R * 8), o_BtB = take(RR * 8), o_dot = take((size_t)R * 8),
                o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
+               o_wcol = take((size_t)R * 8), o_rscale = take((size_t)R * 8),
                o_int = take(16), o_fac = take(host_factors ? sumI * R * 4 : 0);
   char *ws = static_cast<char *>(dalloc(h, off, s));
   if (!ws) return fail(ALTO_ERR_OOM, "CP-ALS workspace of %zu bytes", off);
@@ -1396,6 +1397,7 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
   double *lam_d = host_lambda ? reinterpret_cast<double *>(ws + o_lam) : lambda;
   int *done_at = reinterpret_cast<int *>(ws + o_int);
   int *iters_done_d = done_at + 1;
+  int *renorm_d = done_at + 2;
   float *A[kMaxModes];
   {
     size_t fo = o_fac;
@@ -1425,7 +1427,7 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
     CP_TRY(cudaMemcpyAsync(scl, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, s));
   }
   CP_TRY(cudaMemsetAsync(done_at, 0x7F, sizeof(int), s));
-  CP_TRY(cudaMemsetAsync(iters_done_d, 0, sizeof(int), s));
+  CP_TRY(cudaMemsetAsync(iters_done_d, 0, 2 * sizeof(int), s));  // iterations done, renorm flag
   CP_TRY(cudaMemsetAsync(G, 0, N * RR * 8, s));
   CP_TRY(cudaMemsetAsync(fits_d, 0, (size_t)iters * 8, s));
   for (int m = 0; m < N; ++m) {
@@ -1441,6 +1443,9 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
   ca.BtB = BtB;
   ca.dot = dot;
   ca.W = W;
+  ca.wcol = reinterpret_cast<double *>(ws + o_wcol);
+  ca.rscale = reinterpret_cast<double *>(ws + o_rscale);
+  ca.renorm = renorm_d;
   ca.lambda = lam_d;
   ca.fits = fits_d;
   ca.norm_sq = h->norm_sq_dev;
@@ -1471,6 +1476,7 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
         ProfScope ps(h, ALTO_PROF_SOLVE, s);
         CP_TRY(launch_finish(ca, s));
       }
+      CP_TRY(launch_renorm(A[n], ca.rscale, renorm_d, h->dims[n], R, h->num_sms, s));
     }
     if (tol > 0.0 && it + 1 < iters) {
       int d = INT_MAX;

@@ -1,6 +1,6 @@
 // CP-ALS batch: many CP-ALS runs (Alg. 1) on different tensors advanced
 // together. One step performs one mode update of every active run, as a
-// CUDA graph of four launches:
+// CUDA graph of five launches:
 //   batch_prepare_kernel  per run, fp64: V, Cholesky, W of its current mode
 //                         (Alg. 1, solve); zeroes B^T B and the dot products
 //   group_mttkrp_kernel   the segments of every run (group.cu)
@@ -10,6 +10,8 @@
 //   batch_finish_kernel   per run, fp64: lambda, s_n, G_n, the fit after the
 //                         last mode, the stop test; then (iteration, mode)
 //                         moves on
+//   batch_renorm_kernel   rescales the factor a run just updated when its
+//                         column scales left [2^-20, 2^20] (normally nothing)
 // The runs' states (iteration, mode, stop) live on the device, so one captured
 // graph replays step after step; the host uploads its tables only when runs
 // join or leave, and reads the states back asynchronously.
@@ -35,6 +37,8 @@ struct CpState {
   int iters_done;
   int stopped;      // 1 once the run has ended; every kernel skips it
   uint32_t gen;     // admission number of the run in this slot
+  int renorm;       // this step's mode update asked to renormalise its factor
+  int renorm_mode;  // that mode
   int pad;
 };
 
@@ -42,6 +46,7 @@ struct CpProb {
   float *B[kMaxModes];  // factors B_m (A_m = B_m diag(s_m)) by mode
   float *M;             // MTTKRP output of the current mode, zero between steps
   double *G, *s, *Sn, *BtB, *dot;
+  double *wcol, *rscale;  // column scales of W; renormalisation factors
   float *W;
   double *lambda, *fits;
   const double *norm_sq;
@@ -58,6 +63,9 @@ __device__ __forceinline__ CpArgs make_args(const CpProb &q, CpState &st) {
   a.BtB = q.BtB;
   a.dot = q.dot;
   a.W = q.W;
+  a.wcol = q.wcol;
+  a.rscale = q.rscale;
+  a.renorm = &st.renorm;
   a.lambda = q.lambda;
   a.fits = q.fits;
   a.norm_sq = q.norm_sq;
@@ -82,6 +90,7 @@ __global__ void __launch_bounds__(kUpdThreads) batch_prepare_kernel(const CpProb
     __syncthreads();
     const CpProb &q = probs[p];
     CpState &s = st[p];
+    if (threadIdx.x == 0) s.renorm = 0;  // set again by this step's finish if needed
     if (!q.active || s.stopped) {
       if (threadIdx.x == 0) tiles[p] = 0;
       continue;
@@ -171,6 +180,7 @@ __global__ void __launch_bounds__(kUpdThreads) batch_finish_kernel(const CpProb 
     finish_body(a);
     __syncthreads();
     if (threadIdx.x == 0) {
+      s.renorm_mode = a.n;
       int n = a.n + 1, it = a.it;
       if (n == q.N) {
         n = 0;
@@ -179,6 +189,30 @@ __global__ void __launch_bounds__(kUpdThreads) batch_finish_kernel(const CpProb 
       s.n = n;
       s.it = it;
       if (it >= q.iters || s.done_at <= it) s.stopped = 1;
+    }
+  }
+}
+
+// Every CTA takes its share of the rows of each run whose finish asked for a
+// renormalisation of the factor it just updated: B(:, r) *= rscale[r].
+__global__ void __launch_bounds__(256) batch_renorm_kernel(const CpProb *__restrict__ probs,
+                                                           const CpState *__restrict__ st, const int *nslots) {
+  const int P = *nslots;
+  for (int p = 0; p < P; ++p) {
+    if (!st[p].renorm) continue;
+    const CpProb &q = probs[p];
+    const int n = st[p].renorm_mode, per_row = q.R / 4;
+    const uint64_t total = q.dims[n] * (uint64_t)per_row;
+    float4 *B4 = reinterpret_cast<float4 *>(q.B[n]);
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+      const int c4 = (int)(t % per_row) * 4;
+      float4 v = B4[t];
+      v.x = (float)((double)v.x * q.rscale[c4]);
+      v.y = (float)((double)v.y * q.rscale[c4 + 1]);
+      v.z = (float)((double)v.z * q.rscale[c4 + 2]);
+      v.w = (float)((double)v.w * q.rscale[c4 + 3]);
+      B4[t] = v;
     }
   }
 }
@@ -345,7 +379,7 @@ alto_status configure_kernels() {
   return ALTO_OK;
 }
 
-// One step: the four launches, recorded once into a graph.
+// One step: the five launches, recorded once into a graph.
 cudaError_t enqueue_step(alto_batch *b) {
   cudaStream_t s = b->s;
   const int gp = std::min(b->max_slots, 2 * b->num_sms);
@@ -361,6 +395,9 @@ cudaError_t enqueue_step(alto_batch *b) {
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   batch_finish_kernel<<<gp, kUpdThreads, 0, s>>>(b->cp_dev, b->st_dev, b->nslots_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_renorm_kernel<<<b->num_sms, 256, 0, s>>>(b->cp_dev, b->st_dev, b->nslots_dev);
   return cudaGetLastError();
 }
 
@@ -624,7 +661,8 @@ alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, do
   };
   const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_s = take((size_t)N * R * 8),
                o_Sn = take((size_t)R * 8), o_BtB = take(RR * 8), o_dot = take((size_t)R * 8),
-               o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8);
+               o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
+               o_wcol = take((size_t)R * 8), o_rscale = take((size_t)R * 8);
   size_t o_B[kMaxModes];
   for (int m = 0; m < N; ++m) o_B[m] = take(h->dims[m] * R * 4);
   char *ws = static_cast<char *>(balloc(b, off));
@@ -644,6 +682,8 @@ alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, do
   cp.BtB = reinterpret_cast<double *>(ws + o_BtB);
   cp.dot = reinterpret_cast<double *>(ws + o_dot);
   cp.W = reinterpret_cast<float *>(ws + o_W);
+  cp.wcol = reinterpret_cast<double *>(ws + o_wcol);
+  cp.rscale = reinterpret_cast<double *>(ws + o_rscale);
   cp.fits = reinterpret_cast<double *>(ws + o_fits);
   cp.lambda = reinterpret_cast<double *>(ws + o_lam);
   cp.norm_sq = h->norm_sq_dev;
@@ -715,7 +755,7 @@ alto_status alto_batch_step(alto_batch_t b, int nsteps) {
   if (t0 && t1) CUDA_TRY(cudaEventRecord(t0, b->s));
   for (int i = 0; i < nsteps; ++i) {
     CUDA_TRY(cudaGraphLaunch(b->exec, b->s));
-    note_launches(4);
+    note_launches(5);
   }
   if (t0 && t1) {
     CUDA_TRY(cudaEventRecord(t1, b->s));
@@ -855,7 +895,7 @@ alto_status alto_cpals_footprint(int nmodes, const uint64_t *dims, uint64_t nnz,
   const uint64_t tensor = nnz * (8 * kw + 4) + L * nmodes * 8 + 4096;
   const uint64_t RR = (uint64_t)R * R;
   const uint64_t run = maxI * R * 4 + nmodes * RR * 8 + nmodes * (uint64_t)R * 8 + RR * 20 +
-                       (uint64_t)R * 24 + (uint64_t)iters * 8 + sumI * R * 4 + 4096;
+                       (uint64_t)R * 40 + (uint64_t)iters * 8 + sumI * R * 4 + 4096;
   // encode: the coordinates, the positions and values twice (sort buffers)
   const uint64_t encode = nnz * (4ull * nmodes + 2 * (8 * kw + 4));
   if (resident) *resident = tensor + run;

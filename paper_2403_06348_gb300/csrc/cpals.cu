@@ -274,6 +274,25 @@ __global__ void __launch_bounds__(256) scale_kernel(float *__restrict__ B, const
   }
 }
 
+// B(:, r) *= rscale[r] when finish_body asked for it (its s_n is then 1).
+__global__ void __launch_bounds__(256) renorm_kernel(float *__restrict__ B, const double *__restrict__ rscale,
+                                                     const int *__restrict__ renorm, uint64_t I, int R) {
+  if (!*renorm) return;
+  const int per_row = R / 4;
+  const uint64_t total = I * (uint64_t)per_row;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const int c4 = (int)(t % per_row) * 4;
+    float4 *p = reinterpret_cast<float4 *>(B) + t;
+    float4 v = *p;
+    v.x = (float)((double)v.x * rscale[c4]);
+    v.y = (float)((double)v.y * rscale[c4 + 1]);
+    v.z = (float)((double)v.z * rscale[c4 + 2]);
+    v.w = (float)((double)v.w * rscale[c4 + 3]);
+    *p = v;
+  }
+}
+
 static int grid_rows(uint64_t I, int rows_per_step, int num_sms, int per_sm) {
   uint64_t g = (I + rows_per_step - 1) / rows_per_step;
   const uint64_t cap = (uint64_t)num_sms * per_sm;
@@ -336,6 +355,17 @@ cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, 
     case 32: return launch_update_r<32>(M, W, B, I, BtB, dot, done_at, it, num_sms, s);
     default: return launch_update_r<64>(M, W, B, I, BtB, dot, done_at, it, num_sms, s);
   }
+}
+
+cudaError_t launch_renorm(float *B, const double *rscale, const int *renorm, uint64_t I, int R, int num_sms,
+                          cudaStream_t s) {
+  if (I == 0) return cudaSuccess;
+  const uint64_t total = I * (uint64_t)(R / 4);
+  uint64_t g = (total + 255) / 256;
+  if (g > (uint64_t)num_sms * 8) g = (uint64_t)num_sms * 8;
+  renorm_kernel<<<(unsigned)(g ? g : 1), 256, 0, s>>>(B, rscale, renorm, I, R);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finish(const CpArgs &a, cudaStream_t s) {

@@ -14,7 +14,10 @@ struct CpArgs {
   double *Sn;             // [R] prod_{m != n} s_m of the current mode (kept for the fit)
   const double *BtB;      // [R][R] B_n^T B_n of the new (unnormalised) update
   const double *dot;      // [R] sum_i M_B(i, r) B_n(i, r)
-  float *W;               // [R][R] diag(Sn) V^-1 (fp32)
+  float *W;               // [R][R] diag(Sn) V^-1 diag(1 / wcol) (fp32)
+  double *wcol;           // [R] power-of-two column scales of W (the fp32 W stays in range)
+  double *rscale;         // [R] renormalisation factors of B_n (renorm_kernel)
+  int *renorm;            // nonzero: B_n is to be renormalised (s_n already set to 1)
   double *lambda;         // [R] column norms of the last update
   double *fits;           // [iters]
   const double *norm_sq;  // ||X||^2
@@ -33,6 +36,9 @@ cudaError_t launch_prepare(const CpArgs &a, cudaStream_t s);
 cudaError_t launch_update(const float *M, const float *W, float *B, uint64_t I, int R, double *BtB,
                           double *dot, const int *done_at, int it, int num_sms, cudaStream_t s);
 cudaError_t launch_finish(const CpArgs &a, cudaStream_t s);
+// B(:, r) *= rscale[r] when *renorm is set (finish decided it); else nothing.
+cudaError_t launch_renorm(float *B, const double *rscale, const int *renorm, uint64_t I, int R, int num_sms,
+                          cudaStream_t s);
 cudaError_t launch_scale(float *B, const double *s_m, uint64_t I, int R, int num_sms, cudaStream_t s);
 
 }  // namespace alto

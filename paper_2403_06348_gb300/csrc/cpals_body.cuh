@@ -225,7 +225,30 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     a.Sn[r] = p;
   }
   __syncthreads();
-  for (int e = tid; e < RR; e += nt) a.W[e] = (float)(a.Sn[e >> lgR] * Y[e]);
+  // W = diag(Sn) V^-1 in fp64 (in Y), then stored in fp32 column by column
+  // divided by a power of two near the column's largest entry: Sn multiplies
+  // the other modes' deferred scales and can leave the fp32 range although
+  // the solve is well defined (the scale is undone in fp64 by finish_body).
+  for (int e = tid; e < RR; e += nt) Y[e] *= a.Sn[e >> lgR];
+  __syncthreads();
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int c = tid; c < R; c += nt) {
+    double mx = 0.0;
+    for (int k = 0; k < R; ++k) mx = fmax(mx, fabs(Y[k * R + c]));
+    if (!isfinite(mx)) bad = 1;
+    a.wcol[c] = (mx > 0.0 && isfinite(mx)) ? ldexp(1.0, ilogb(mx)) : 1.0;
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) {
+      atomicOr(a.status, kStatusNotSpd);
+      *a.done_at = a.it;
+    }
+    return;
+  }
+  for (int e = tid; e < RR; e += nt) a.W[e] = (float)(Y[e] / a.wcol[e & (R - 1)]);
 }
 
 // B = M W with B^T B and the column dot products of M and B, one pass.
@@ -412,11 +435,26 @@ __device__ __forceinline__ void finish_body(const CpArgs &a) {
   __shared__ double part[2][256];
   double *sv = a.s + (size_t)a.n * R;
   double *Gn = a.G + (size_t)a.n * RR;
+  // the stored B_n is the solution with column r divided by wcol[r]:
+  // lambda_r = wcol[r] ||B_n(:, r)||, and A_n(:, r) = B_n(:, r) / ||B_n(:, r)||
+  __shared__ double bn[ALTO_MAX_RANK];
+  __shared__ int flags;  // bit 0: non-finite update, bit 1: renormalise B_n
+  if (tid == 0) flags = 0;
+  __syncthreads();
   for (int r = tid; r < R; r += blockDim.x) {
     const double g = a.BtB[r * R + r];
-    lam[r] = g > 0.0 ? sqrt(g) : 0.0;
+    if (!isfinite(g)) atomicOr(&flags, 1);
+    bn[r] = g > 0.0 ? sqrt(g) : 0.0;
+    lam[r] = bn[r] * a.wcol[r];
   }
   __syncthreads();
+  if (flags & 1) {  // the update left the fp32 range: the run ends here
+    if (tid == 0) {
+      atomicOr(a.status, kStatusNotSpd);
+      *a.done_at = a.it;
+    }
+    return;
+  }
   // a column of rounding noise (norm at most 1e-12 of the largest, left by a
   // pseudo-inverse solve) is a zero column: lambda_r = 0 and s_r = 0
   double lmax = 0.0;
@@ -426,12 +464,20 @@ __device__ __forceinline__ void finish_body(const CpArgs &a) {
     double l = lam[r];
     if (!(l > 1e-12 * lmax)) l = 0.0;
     lam[r] = l;
-    sn[r] = l > 0.0 ? 1.0 / l : 0.0;
+    sn[r] = l > 0.0 ? 1.0 / bn[r] : 0.0;
     a.lambda[r] = l;
-    sv[r] = sn[r];
+    // scales far from 1 would let the deferred normalisation drift out of
+    // the fp32 range over the iterations: renormalise B_n (renorm_kernel)
+    if (sn[r] != 0.0 && (sn[r] > 0x1p20 || sn[r] < 0x1p-20)) atomicOr(&flags, 2);
   }
   __syncthreads();
   for (int e = tid; e < RR; e += blockDim.x) Gn[e] = a.BtB[e] * sn[e / R] * sn[e % R];
+  const bool renorm = (flags & 2) != 0 && a.rscale != nullptr;
+  for (int r = tid; r < R; r += blockDim.x) {
+    if (renorm) a.rscale[r] = sn[r];
+    sv[r] = renorm ? (sn[r] != 0.0 ? 1.0 : 0.0) : sn[r];
+  }
+  if (tid == 0 && a.renorm) *a.renorm = renorm ? 1 : 0;
   __syncthreads();
   if (!a.last_mode) return;
   // fit = 1 - sqrt(max(0, ||X||^2 + lam^T (*_m G_m) lam - 2 <X, X_hat>)) / ||X||,
@@ -442,7 +488,7 @@ __device__ __forceinline__ void finish_body(const CpArgs &a) {
     for (int m = 0; m < a.N; ++m) h *= a.G[(size_t)m * RR + e];
     s1 += lam[e / R] * lam[e % R] * h;
   }
-  for (int r = tid; r < R; r += blockDim.x) s2 += a.Sn[r] * a.dot[r];
+  for (int r = tid; r < R; r += blockDim.x) s2 += a.Sn[r] * a.wcol[r] * a.dot[r];
   part[0][tid] = s1;
   part[1][tid] = s2;
   __syncthreads();
