@@ -387,9 +387,20 @@ def tensor_norm_sq(coords: np.ndarray, vals: np.ndarray) -> float:
     squared and summed."""
     if coords.shape[1] == 0:
         return 0.0
-    _, inv = np.unique(np.asarray(coords).T, axis=0, return_inverse=True)
-    cells = np.zeros(int(inv.max()) + 1)
-    np.add.at(cells, inv.ravel(), np.asarray(vals, dtype=np.float64))
+    coords = np.asarray(coords)
+    # identify equal coordinates: one integer per nonzero (the coordinates
+    # side by side) when they fit 64 bits, else the rows of coords.T
+    widths = [max(int(c.max()), 1).bit_length() for c in coords]
+    if sum(widths) <= 64:
+        key = np.zeros(coords.shape[1], dtype=np.uint64)
+        shift = 0
+        for c, w in zip(coords, widths):
+            key |= c.astype(np.uint64) << np.uint64(shift)
+            shift += w
+        _, inv = np.unique(key, return_inverse=True)
+    else:
+        _, inv = np.unique(coords.T, axis=0, return_inverse=True)
+    cells = np.bincount(inv.ravel(), weights=np.asarray(vals, dtype=np.float64))
     return float(np.sum(cells * cells))
 
 

@@ -123,3 +123,26 @@ def test_non_finite_factors_report_not_spd():
     # the handle stays usable
     A2 = gu.gpu_factors(gu.rand_factors(dims, 4, 7))
     t.cpals(4, 2, A2)
+
+
+@pytest.mark.slow
+def test_full_size_first_iteration_fit():
+    """Iteration 1 of Alg. 1 (every mode update, then the fit) on the
+    1e8-nonzero Zipf tensor 10M x 2M x 50k at R = 32, the bench's workload:
+    the GPU's fit equals the oracle's (fp64 solve, C fp64 MTTKRP) within 1e-4."""
+    import os
+    from oracle import cref
+    spec = synth.ZIPF3D
+    coords, vals = synth.cached(spec)
+    coords = np.asarray(coords)
+    vals = np.asarray(vals)
+    init = synth.factors(spec.dims, spec.rank, seed=1)
+    t = gu.encode(coords, vals, spec.dims)
+    A = gu.gpu_factors(init)
+    _, fits = t.cpals(spec.rank, 1, A)
+    t.free()
+    del A
+    nt = os.cpu_count() or 1
+    ref = ar.cp_als(coords, vals, spec.dims, init, 1,
+                    mttkrp_fn=lambda c, v, F, n: cref.mttkrp(c, v, spec.dims, F, n, nthreads=nt))
+    assert abs(fits[0] - ref.fits[0]) <= 1e-4, (fits[0], ref.fits[0])
