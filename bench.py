@@ -231,9 +231,11 @@ def time_modes(h, Ad, R, dims, reps=5):
         for _ in range(reps):
             h.mttkrp(n, Ad, R, out=o)
         torch.cuda.synchronize()
-        launches, ms = h.profile_read(reset=True)["mttkrp"]
+        pr = h.profile_read(reset=True)
+        launches, ms = pr["mttkrp"]
+        zms = pr.get("zero", (0, 0.0))[1]
         h.profile_enable(False)
-        res.append((ms / max(reps, 1), h.get_mode_plan(n, R)))
+        res.append((ms / max(reps, 1), h.get_mode_plan(n, R), zms / max(reps, 1)))
     del out
     return res
 
@@ -265,10 +267,10 @@ def config_entry(spec, coords, dims, R, kw, timed, fbytes, peak):
     bytes_mode, _ = algorithmic_bytes_per_mode(coords, dims, R, 8 * kw, fbytes)
     M = coords.shape[1]
     modes = []
-    for n, (ms, plan) in enumerate(timed):
+    for n, (ms, plan, zms) in enumerate(timed):
         gbs = bytes_mode[n] / (ms / 1e3) / 1e9 if ms > 0 else 0.0
         modes.append({"mode": n, "rows": int(dims[n]), "plan": VARIANT_NAMES.get(plan[0], plan[0]),
-                      "cols_per_lane": plan[1], "staged_rows": plan[2], "ms": ms,
+                      "cols_per_lane": plan[1], "staged_rows": plan[2], "ms": ms, "zeroing_ms": zms,
                       "nnz_r_per_s": M * R / (ms / 1e3) if ms > 0 else None,
                       "algorithmic_bytes": bytes_mode[n], "gbs": gbs, "frac": gbs / peak})
     tot_ms = sum(m["ms"] for m in modes)
@@ -523,6 +525,9 @@ def run_ours(args):
               "mttkrp_kernel" if not any(outorder) else "mttkrp_out_kernel + mttkrp_kernel")
     n_mttkrp, ms_mttkrp = prof.get("mttkrp", (0, 0.0))
     avg_ms = ms_mttkrp / max(n_mttkrp, 1)
+    # the output rows are counted as written once; the separate zeroing
+    # launch writes every one of them, so the fraction with it is also given
+    avg_ms_zero = (ms_mttkrp + prof.get("zero", (0, 0.0))[1]) / max(n_mttkrp, 1)
     avg_bytes = sum(bytes_per_mode) / N
     achieved = avg_bytes / (avg_ms / 1000.0) / 1e9 if avg_ms > 0 else 0.0
     peak, peak_src = measured_peaks()
@@ -543,6 +548,8 @@ def run_ours(args):
                          "peak_source": f"{peak_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": avg_bytes,
                          "avg_launch_ms": avg_ms, "launches": n_mttkrp,
+                         "frac_incl_output_zeroing": (avg_bytes / (avg_ms_zero / 1e3) / 1e9 / peak
+                                                      if avg_ms_zero > 0 else None),
                          "source_sha": sha},
             "gpu_launches": launches,
             "clocks": clocks,
