@@ -11,7 +11,7 @@
 //                         last mode, the stop test; then (iteration, mode)
 //                         moves on
 //   batch_renorm_kernel   rescales the factor a run just updated when its
-//                         column scales left [2^-20, 2^20] (normally nothing)
+//                         column norms left the range finish_body allows
 // The runs' states (iteration, mode, stop) live on the device, so one captured
 // graph replays step after step; the host uploads its tables only when runs
 // join or leave, and reads the states back asynchronously.
@@ -208,10 +208,10 @@ __global__ void __launch_bounds__(256) batch_renorm_kernel(const CpProb *__restr
          t += (uint64_t)gridDim.x * blockDim.x) {
       const int c4 = (int)(t % per_row) * 4;
       float4 v = B4[t];
-      v.x = (float)((double)v.x * q.rscale[c4]);
-      v.y = (float)((double)v.y * q.rscale[c4 + 1]);
-      v.z = (float)((double)v.z * q.rscale[c4 + 2]);
-      v.w = (float)((double)v.w * q.rscale[c4 + 3]);
+      v.x *= (float)q.rscale[c4];
+      v.y *= (float)q.rscale[c4 + 1];
+      v.z *= (float)q.rscale[c4 + 2];
+      v.w *= (float)q.rscale[c4 + 3];
       B4[t] = v;
     }
   }

@@ -285,10 +285,10 @@ __global__ void __launch_bounds__(256) renorm_kernel(float *__restrict__ B, cons
     const int c4 = (int)(t % per_row) * 4;
     float4 *p = reinterpret_cast<float4 *>(B) + t;
     float4 v = *p;
-    v.x = (float)((double)v.x * rscale[c4]);
-    v.y = (float)((double)v.y * rscale[c4 + 1]);
-    v.z = (float)((double)v.z * rscale[c4 + 2]);
-    v.w = (float)((double)v.w * rscale[c4 + 3]);
+    v.x *= (float)rscale[c4];
+    v.y *= (float)rscale[c4 + 1];
+    v.z *= (float)rscale[c4 + 2];
+    v.w *= (float)rscale[c4 + 3];
     *p = v;
   }
 }

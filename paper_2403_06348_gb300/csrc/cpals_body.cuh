@@ -225,10 +225,12 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     a.Sn[r] = p;
   }
   __syncthreads();
-  // W = diag(Sn) V^-1 in fp64 (in Y), then stored in fp32 column by column
-  // divided by a power of two near the column's largest entry: Sn multiplies
-  // the other modes' deferred scales and can leave the fp32 range although
-  // the solve is well defined (the scale is undone in fp64 by finish_body).
+  // W = diag(Sn) V^-1 in fp64 (in Y), stored in fp32. Sn multiplies the
+  // other modes' deferred scales and can leave the fp32 range although the
+  // solve is well defined: a column whose largest entry is outside
+  // [2^-60, 2^60] is divided by a power of two near it (undone in fp64 by
+  // finish_body). Other columns keep scale 1, so that B_n = M V^-1 keeps its
+  // natural magnitude (the column norms lambda).
   for (int e = tid; e < RR; e += nt) Y[e] *= a.Sn[e >> lgR];
   __syncthreads();
   __shared__ int bad;
@@ -238,7 +240,7 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     double mx = 0.0;
     for (int k = 0; k < R; ++k) mx = fmax(mx, fabs(Y[k * R + c]));
     if (!isfinite(mx)) bad = 1;
-    a.wcol[c] = (mx > 0.0 && isfinite(mx)) ? ldexp(1.0, ilogb(mx)) : 1.0;
+    a.wcol[c] = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ldexp(1.0, ilogb(mx)) : 1.0;
   }
   __syncthreads();
   if (bad) {
@@ -460,15 +462,19 @@ __device__ __forceinline__ void finish_body(const CpArgs &a) {
   double lmax = 0.0;
   for (int r = 0; r < R; ++r) lmax = fmax(lmax, lam[r]);
   __syncthreads();
+  // Column norms of B_n far from 1 would let the deferred normalisation
+  // drift out of the fp32 range over the iterations (the MTTKRP multiplies
+  // the other N - 1 factors' entries): outside [2^-e, 2^e], with
+  // e = min(60, 90 / (N - 1)), B_n is renormalised (renorm_kernel).
+  const double elim = a.N > 1 ? fmin(60.0, floor(90.0 / (a.N - 1))) : 60.0;
+  const double hi = ldexp(1.0, (int)elim), lo = ldexp(1.0, -(int)elim);
   for (int r = tid; r < R; r += blockDim.x) {
     double l = lam[r];
     if (!(l > 1e-12 * lmax)) l = 0.0;
     lam[r] = l;
     sn[r] = l > 0.0 ? 1.0 / bn[r] : 0.0;
     a.lambda[r] = l;
-    // scales far from 1 would let the deferred normalisation drift out of
-    // the fp32 range over the iterations: renormalise B_n (renorm_kernel)
-    if (sn[r] != 0.0 && (sn[r] > 0x1p20 || sn[r] < 0x1p-20)) atomicOr(&flags, 2);
+    if (sn[r] != 0.0 && (sn[r] > hi || sn[r] < lo)) atomicOr(&flags, 2);
   }
   __syncthreads();
   for (int e = tid; e < RR; e += blockDim.x) Gn[e] = a.BtB[e] * sn[e / R] * sn[e % R];
