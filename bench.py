@@ -59,6 +59,10 @@ def parse_args():
                    help="skip the per-mode MTTKRP measurements of the other workloads")
     p.add_argument("--configs-scale", type=float, default=1.0,
                    help="scale the nonzeros of the other workloads (testing only)")
+    p.add_argument("--profile-mttkrp", default="",
+                   choices=["", "uniform3d", "zipf3d", "count4d", "zipf5d"],
+                   help="profiling aid: encode this workload (--nnz scales it), run one MTTKRP "
+                        "per mode with --plans (default plans if none) and exit")
     return p.parse_args()
 
 
@@ -730,10 +734,42 @@ def run_e2e(args, alto, coords, vals, spec, A0, world, barrier, plans=None):
             "steps": steps}
 
 
+def run_profile_mttkrp(args):
+    """One MTTKRP per mode of a named workload, for an ncu capture of the
+    MTTKRP kernels alone (no tuning launches before them)."""
+    import torch
+    import paper_2403_06348_gb300 as alto
+    import synth
+    spec = {"uniform3d": synth.UNIFORM3D, "zipf3d": synth.ZIPF3D, "count4d": synth.COUNT4D,
+            "zipf5d": synth.ZIPF5D}[args.profile_mttkrp]
+    if args.nnz:
+        spec = synth.scaled(spec, args.nnz)
+    alto.build()
+    coords, vals = synth.cached(spec)
+    coords = np.asarray(coords)
+    vals = np.asarray(vals)
+    h = alto.alto_encode(torch.from_numpy(coords.view(np.int32)).cuda(), torch.from_numpy(vals).cuda(),
+                         spec.dims)
+    R = spec.rank
+    A = [torch.from_numpy(a).cuda() for a in synth.factors(spec.dims, R, seed=1)]
+    plans = [tuple(int(v) for v in x.split(":")) for x in args.plans.split(",")] if args.plans else []
+    out = torch.empty((max(spec.dims), R), dtype=torch.float32, device="cuda")
+    for n in range(len(spec.dims)):
+        if n < len(plans):
+            h.set_mode_plan(n, plans[n][0], plans[n][1])
+        h.mttkrp(n, A, R, out=out[:spec.dims[n]])
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": spec.name, "plans": [h.get_mode_plan(n, R) for n in range(len(spec.dims))]}))
+    h.free()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_mttkrp:
+        return run_profile_mttkrp(args)
     return run_ours(args)
 
 
