@@ -498,11 +498,15 @@ def run_ours(args):
             for k, (n, ms) in h.profile_read().items():
                 a, b = profile_into.get(k, (0, 0.0))
                 profile_into[k] = (a + n, b + ms)
-        info_kw = None
-        if profile_into is not None and "_kw" not in profile_into:
+        if profile_into is not None:
             info = h.query()
-            profile_into["_kw"] = int(info.key_words)
-            profile_into["_plans"] = [h.get_mode_plan(n, R) for n in range(N)]
+            enc = profile_into.setdefault("_encode", [0.0, 0.0, 0])
+            enc[0] += info.encode_ms
+            enc[1] += info.sort_ms
+            enc[2] = int(info.sort_passes)
+            if "_kw" not in profile_into:
+                profile_into["_kw"] = int(info.key_words)
+                profile_into["_plans"] = [h.get_mode_plan(n, R) for n in range(N)]
         h.free()
         return fits
 
@@ -575,6 +579,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "breakdown_ms_per_step": breakdown,
+            "encode": encode_line(prof, M, kw, args.steps, peak),
             "final_fit": fits[-1] if fits else None}
 
     if not args.no_e2e:
@@ -768,6 +773,20 @@ def run_e2e(args, alto, coords, vals, spec, A0, world, barrier, plans=None):
     return {"value": job_value(ITERS * N * M * R, world, ms), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ms,
             "steps": steps}
+
+
+def encode_line(prof, M, kw, steps, peak):
+    """The encode's device time per step and the radix sort's bandwidth: per
+    8-bit pass the positions and values are read and written once, and the
+    digit counts of all passes take one more read of the positions."""
+    enc_ms, sort_ms, passes = prof.get("_encode", [0.0, 0.0, 0])
+    enc_ms, sort_ms = enc_ms / steps, sort_ms / steps
+    sort_bytes = M * passes * (2 * 8 * kw + 2 * 4) + M * 8 * kw
+    gbs = sort_bytes / (sort_ms / 1e3) / 1e9 if sort_ms > 0 else 0.0
+    return {"ms_per_step": enc_ms, "sort_ms": sort_ms, "sort_passes": passes,
+            "sort_bytes": sort_bytes, "sort_gbs": gbs, "sort_frac": gbs / peak,
+            "bytes_model": "M*(passes*(2*8*kw + 2*4) + 8*kw): positions and values read "
+                           "and written once per pass, plus one read for the digit counts"}
 
 
 def run_profile_mttkrp(args):

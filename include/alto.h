@@ -126,6 +126,15 @@ typedef struct alto_info {
   uint32_t nhot[ALTO_MAX_MODES];      /* hot rows found per mode                    */
   double norm_sq;                     /* ||X||^2 = sum of squared values            */
   size_t device_bytes;                /* device memory held by the handle           */
+  float encode_ms;                    /* device time of alto_encode's kernels, from
+                                         the first (linearize) to the last (hot
+                                         rows), CUDA events on the encode stream   */
+  float sort_ms;                      /* of which the radix sort (digit counts and
+                                         every pass; the one host read of the
+                                         digit counts included)                    */
+  int sort_passes;                    /* 8-bit radix passes launched: passes whose
+                                         digit is the same for every nonzero are
+                                         left out                                  */
 } alto_info;
 
 /* Per-mode MTTKRP plan (what the autotuner sets). */

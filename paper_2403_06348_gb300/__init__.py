@@ -54,7 +54,8 @@ class alto_info(ctypes.Structure):
                 ("mask_hi", ctypes.c_uint64 * ALTO_MAX_MODES),
                 ("max_interval", ctypes.c_uint32 * ALTO_MAX_MODES),
                 ("nhot", ctypes.c_uint32 * ALTO_MAX_MODES), ("norm_sq", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("encode_ms", ctypes.c_float),
+                ("sort_ms", ctypes.c_float), ("sort_passes", ctypes.c_int)]
 
 
 PROF_KINDS = ("mttkrp", "pull_reduce", "zero", "gram", "solve", "rmul", "pos_out")

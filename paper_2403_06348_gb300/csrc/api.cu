@@ -992,24 +992,24 @@ alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_
   bool own_coords = false, own_vals = false;
   uint64_t *kbuf[2] = {nullptr, nullptr};
   float *vbuf[2] = {nullptr, nullptr};
-  uint32_t *table = nullptr, *table_scan = nullptr, *block_sums = nullptr;
+  void *sort_work = nullptr;
   uint32_t *counts = nullptr, *hot_scratch = nullptr;
   uint32_t **counts_ptrs_dev = nullptr;
   uint64_t *hot_list = nullptr;
   uint64_t sum_dims = 0;
   for (int n = 0; n < N; ++n) sum_dims += dims[n];
-  const size_t entries = sort_table_entries(M);
-  const size_t nblocks = sort_scan_blocks(M);
+  const size_t sort_bytes = sort_workspace_bytes(M);
+  cudaEvent_t evs[4] = {};  // encode start, sort start, sort end, encode end
   auto cleanup = [&]() {
+    for (cudaEvent_t &ev : evs)
+      if (ev) cudaEventDestroy(ev), ev = nullptr;
     if (own_coords) dfree(h, coords_d, (size_t)N * M * 4, s);
     if (own_vals) dfree(h, vals_d, M * 4, s);
     for (int b = 0; b < 2; ++b) {
       if (kbuf[b] && kbuf[b] != h->keys) dfree(h, kbuf[b], M * kw * 8, s);
       if (vbuf[b] && vbuf[b] != h->vals) dfree(h, vbuf[b], M * 4, s);
     }
-    dfree(h, table, entries * 4, s);
-    dfree(h, table_scan, entries * 4, s);
-    dfree(h, block_sums, std::max<size_t>(nblocks, 1) * 4, s);
+    dfree(h, sort_work, sort_bytes, s);
     dfree(h, counts, sum_dims * 4, s);
     dfree(h, hot_scratch, 64 * 4, s);
     dfree(h, counts_ptrs_dev, kMaxModes * sizeof(void *), s);
@@ -1040,17 +1040,20 @@ alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_
     if ((st = alloc_n(h, &kbuf[b], (size_t)M * kw, s, "keys")) != ALTO_OK) return bail2(st);
     if ((st = alloc_n(h, &vbuf[b], M, s, "values")) != ALTO_OK) return bail2(st);
   }
-  if ((st = alloc_n(h, &table, entries, s, "sort table")) != ALTO_OK) return bail2(st);
-  if ((st = alloc_n(h, &table_scan, entries, s, "sort offsets")) != ALTO_OK) return bail2(st);
-  if ((st = alloc_n(h, &block_sums, std::max<size_t>(nblocks, 1), s, "scan sums")) != ALTO_OK)
-    return bail2(st);
+  if (M > 0 && !(sort_work = dalloc(h, sort_bytes, s))) return bail2(fail(ALTO_ERR_OOM, "sort workspace"));
 
+  for (cudaEvent_t &ev : evs)
+    if (cudaEventCreate(&ev) != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "encode events"));
+  cudaEventRecord(evs[0], s);
   cudaError_t e = launch_linearize(h->dp, coords_d, M, h->dims_dev, kbuf[0], h->status_dev,
                                    h->num_sms, s);
   if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "linearize: %s", cudaGetErrorString(e)));
   int fb = 0;
-  e = launch_radix_sort(kw, h->nbits, M, kbuf, vbuf, vals_d, table, table_scan, block_sums, &fb, s);
+  cudaEventRecord(evs[1], s);
+  e = launch_radix_sort(kw, h->nbits, M, kbuf, vbuf, vals_d, sort_work, h->status_dev, true, &fb,
+                        &h->sort_passes, h->num_sms, s);
   if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "radix sort: %s", cudaGetErrorString(e)));
+  cudaEventRecord(evs[2], s);
   h->keys = kbuf[fb];
   h->vals = vbuf[fb];
   {
@@ -1093,6 +1096,7 @@ alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_
     if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "hot rows: %s", cudaGetErrorString(e)));
   }
   uint32_t status = 0;
+  cudaEventRecord(evs[3], s);
   if (cudaMemcpyAsync(&status, h->status_dev, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(&h->norm_sq, h->norm_sq_dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(h->nhot, h->nhot_dev, kMaxModes * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -1100,6 +1104,10 @@ alto_status alto_encode(const uint32_t *coords, const float *vals, const uint64_
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail2(fail(ALTO_ERR_CUDA, "encode: %s", cudaGetErrorString(e)));
   if (status & kStatusCoordRange) return bail2(fail(ALTO_ERR_COORD_RANGE, "coordinate >= dims"));
+  if (status & kStatusTimeout) return bail2(fail(ALTO_ERR_TIMEOUT, "radix sort: a look-back wait expired"));
+  if (cudaEventElapsedTime(&h->encode_ms, evs[0], evs[3]) != cudaSuccess ||
+      cudaEventElapsedTime(&h->sort_ms, evs[1], evs[2]) != cudaSuccess)
+    return bail2(fail(ALTO_ERR_CUDA, "encode timing"));
   for (int n = 0; n < N; ++n) {
     h->hot_host[n].resize(h->nhot[n]);
     if (h->nhot[n] &&
@@ -1209,6 +1217,9 @@ alto_status alto_query(alto_handle_t h, alto_info *info) {
   }
   info->norm_sq = h->norm_sq;
   info->device_bytes = h->bytes_held;
+  info->encode_ms = h->encode_ms;
+  info->sort_ms = h->sort_ms;
+  info->sort_passes = h->sort_passes;
   return ALTO_OK;
 }
 

@@ -3,6 +3,9 @@
 // the ATOMIC MTTKRP variant.
 #include "encode.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace alto {
 
 // ---------------------------------------------------------------------------
@@ -142,15 +145,30 @@ __global__ void __launch_bounds__(256) norm_span_kernel(const double *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort of (position, value) pairs, 8-bit digits,
-// reduce-then-scan per pass: upsweep (per-tile digit counts), exclusive scan
-// of the digit-major count table, downsweep (stable local ranks, staged in
-// shared memory, coalesced write-out). No inter-CTA waiting anywhere.
+// Stable LSD radix sort of (position, value) pairs with 8-bit digits.
+// One histogram kernel reads the positions once and counts the digits of
+// every pass. Then one kernel per pass ranks each tile of 4096 items in
+// shared memory, finds the tile's first output slot per digit by a chained
+// scan over the tiles (each tile publishes its own digit counts, then looks
+// back over its predecessors until it meets a running total, and publishes
+// its own), and writes the tile out through shared memory, one digit run
+// after the other. Tiles are handed out in start order through a ticket
+// counter, so a tile only waits on tiles whose CTAs already run; every wait
+// is bounded (2 s) and reports kStatusTimeout.
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
 constexpr int kRadix = 256;
+constexpr int kMaxSortPasses = 16;                     // 128-bit positions
+constexpr int kHistItems = 8;
+constexpr uint64_t kLookLimitNs = 2000000000ull;
+constexpr int kLookWindow = 8;
+
+// look-back word: bits 63-62 kind (1 = the tile's own count, 2 = running
+// total through the tile), bits 61-56 the pass (1-based), bits 31-0 the count
+constexpr uint64_t kLookOwn = 1ull << 62;
+constexpr uint64_t kLookTotal = 2ull << 62;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -158,40 +176,73 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-template <int KW>
-__global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint64_t *__restrict__ keys,
-                                                             uint64_t nnz, int word, int shift,
-                                                             uint32_t ntiles,
-                                                             uint32_t *__restrict__ table) {
-  __shared__ uint32_t hist[kRadix];
-  const uint32_t t = blockIdx.x;
-  hist[threadIdx.x] = 0;
-  __syncthreads();
-  const uint64_t base = (uint64_t)t * kSortTile;
-  // all of the thread's digits first (16 loads in flight), then the counts
-  uint32_t dig[kSortItems];
+// lanes of the warp holding the same digit (d < 512; 256 marks "no item"):
+// nine ballots, one per bit, intersected
+__device__ __forceinline__ unsigned digit_peers(uint32_t d) {
+  unsigned m = 0xffffffffu;
 #pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint64_t x = base + (uint64_t)i * kSortThreads + threadIdx.x;
-    dig[i] = x < nnz ? (uint32_t)((keys[x * KW + word] >> shift) & 0xFFu) : kRadix;
+  for (int b = 0; b < 9; ++b) {
+    const bool set = (d >> b) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, set);
+    m &= set ? bal : ~bal;
   }
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint32_t d = dig[i];
-    const bool valid = d < kRadix;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    if (valid && (peers & lanemask_lt()) == 0) atomicAdd(&hist[d], (uint32_t)__popc(peers));
-  }
-  __syncthreads();
-  table[(uint64_t)threadIdx.x * ntiles + t] = hist[threadIdx.x];
+  return m;
 }
 
-// --- exclusive scan of a uint32 table (values and total < 2^32) ------------
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanBlock = kScanThreads * kScanItems;
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t sort_clock_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <int KW>
+__device__ __forceinline__ uint32_t sort_digit(const uint64_t (&k)[KW], int bit) {
+  const uint64_t kd = (KW == 2 && bit >= 64) ? k[KW - 1] : k[0];
+  return (uint32_t)((kd >> (bit & 63)) & 0xFFu);
+}
+
+// hist[p * 256 + d] += number of positions whose digit p is d, p < passes.
+// One shared-memory atomic per digit: the counts need no ranks, and peers
+// found by ballots cost more issue slots than the atomics' conflicts.
+template <int KW>
+__global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(const uint64_t *__restrict__ keys,
+                                                                  uint64_t nnz, int passes,
+                                                                  uint32_t *__restrict__ hist) {
+  __shared__ uint32_t sh[kMaxSortPasses * kRadix];
+  for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads) sh[i] = 0;
+  __syncthreads();
+  const uint64_t step = (uint64_t)gridDim.x * kSortThreads * kHistItems;
+  for (uint64_t base = (uint64_t)blockIdx.x * kSortThreads * kHistItems; base < nnz; base += step) {
+    uint64_t k[kHistItems][KW];
+#pragma unroll
+    for (int i = 0; i < kHistItems; ++i) {
+      const uint64_t x = base + (uint64_t)i * kSortThreads + threadIdx.x;
+#pragma unroll
+      for (int w = 0; w < KW; ++w) k[i][w] = x < nnz ? __ldcs(keys + x * KW + w) : 0ull;
+    }
+#pragma unroll
+    for (int i = 0; i < kHistItems; ++i) {
+      if (base + (uint64_t)i * kSortThreads + threadIdx.x >= nnz) continue;
+      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * kRadix + sort_digit<KW>(k[i], 8 * p)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += kSortThreads)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// --- exclusive scan over the block (values and total < 2^32) ---------------
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v) {
   __shared__ uint32_t warp_sums[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t inc = v;
@@ -214,105 +265,53 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *t
   }
   __syncthreads();
   const uint32_t warp_prefix = warp ? warp_sums[warp - 1] : 0u;
-  if (total) *total = warp_sums[((blockDim.x + 31) >> 5) - 1];
   __syncthreads();
   return warp_prefix + inc - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_reduce(const uint32_t *__restrict__ in,
-                                                            uint64_t n,
-                                                            uint32_t *__restrict__ sums) {
-  const uint64_t base = (uint64_t)blockIdx.x * kScanBlock;
-  uint32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const uint64_t x = base + (uint64_t)i * kScanThreads + threadIdx.x;
-    if (x < n) s += in[x];
-  }
-  uint32_t total;
-  block_exclusive_scan(s, &total);
-  if (threadIdx.x == 0) sums[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_top(uint32_t *__restrict__ sums, uint32_t n) {
-  // single block: exclusive scan of n block sums in place
-  const uint32_t per = (n + kScanThreads - 1) / kScanThreads;
-  const uint32_t b = threadIdx.x * per;
-  uint32_t s = 0;
-  for (uint32_t i = 0; i < per && b + i < n; ++i) s += sums[b + i];
-  uint32_t run = block_exclusive_scan(s, nullptr);
-  for (uint32_t i = 0; i < per && b + i < n; ++i) {
-    const uint32_t v = sums[b + i];
-    sums[b + i] = run;
-    run += v;
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_down(const uint32_t *__restrict__ in, uint64_t n,
-                                                          const uint32_t *__restrict__ sums,
-                                                          uint32_t *__restrict__ out) {
-  const uint64_t base = (uint64_t)blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanItems;
-  uint32_t v[kScanItems];
-  uint32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    v[i] = (base + i < n) ? in[base + i] : 0u;
-    s += v[i];
-  }
-  uint32_t run = block_exclusive_scan(s, nullptr) + sums[blockIdx.x];
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    if (base + i < n) out[base + i] = run;
-    run += v[i];
-  }
-}
-
+// One pass: digit (keys >> bit) & 0xFF of every position, stable.
+// hist = this pass's 256 digit counts; look = ntiles x 256 words, zero or
+// left by other passes; ticket = this pass's counter, zero.
 template <int KW>
-struct SortItem {
-  uint64_t k[KW];
-};
-
-template <int KW>
-__global__ void __launch_bounds__(kSortThreads) radix_downsweep(
-    const uint64_t *__restrict__ keys_in, const float *__restrict__ vals_in, uint64_t nnz,
-    int word, int shift, uint32_t ntiles, const uint32_t *__restrict__ offsets,
-    uint64_t *__restrict__ keys_out, float *__restrict__ vals_out) {
+__global__ void __launch_bounds__(kSortThreads, 2) radix_pass_kernel(
+    const uint64_t *__restrict__ keys_in, const float *__restrict__ vals_in, uint64_t nnz, int bit,
+    uint32_t pass_tag, const uint32_t *__restrict__ hist, uint64_t *look, uint32_t *ticket,
+    uint32_t *status, uint64_t *__restrict__ keys_out, float *__restrict__ vals_out) {
   extern __shared__ __align__(16) unsigned char sm[];
   uint64_t *sk = reinterpret_cast<uint64_t *>(sm);                         // kSortTile * KW
   float *sv = reinterpret_cast<float *>(sk + (size_t)kSortTile * KW);     // kSortTile
   uint32_t *wcount = reinterpret_cast<uint32_t *>(sv + kSortTile);        // 8 * 256
   uint32_t *dstart = wcount + 8 * kRadix;                                  // 256
   uint32_t *gbase = dstart + kRadix;                                       // 256
+  __shared__ uint32_t s_tile;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t t = blockIdx.x;
-  const uint64_t tile_base = (uint64_t)t * kSortTile;
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
   for (int i = threadIdx.x; i < 8 * kRadix; i += kSortThreads) wcount[i] = 0;
-  gbase[threadIdx.x] = offsets[(uint64_t)threadIdx.x * ntiles + t];
   __syncthreads();
+  const uint32_t t = s_tile;
+  const uint64_t tile_base = (uint64_t)t * kSortTile;
 
   // warp w owns items [w*512, w*512+512) of the tile, in 16 rounds of 32
   uint64_t k[kSortItems][KW];
   float v[kSortItems];
   uint32_t rank[kSortItems];
   uint32_t dig[kSortItems];
-  // all of the thread's items first (loads in flight together), then the ranks
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const uint64_t x = tile_base + (uint64_t)warp * (32 * kSortItems) + r * 32 + lane;
     const bool valid = x < nnz;
 #pragma unroll
-    for (int w = 0; w < KW; ++w) k[r][w] = valid ? keys_in[x * KW + w] : 0ull;
-    v[r] = valid ? vals_in[x] : 0.f;
+    for (int w = 0; w < KW; ++w) k[r][w] = valid ? __ldcs(keys_in + x * KW + w) : 0ull;
+    v[r] = valid ? __ldcs(vals_in + x) : 0.f;
   }
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const uint64_t x = tile_base + (uint64_t)warp * (32 * kSortItems) + r * 32 + lane;
     const bool valid = x < nnz;
-    const uint64_t kd = (KW == 2 && word) ? k[r][KW - 1] : k[r][0];
-    const uint32_t d = valid ? (uint32_t)((kd >> shift) & 0xFFu) : kRadix;
+    const uint32_t d = valid ? sort_digit<KW>(k[r], bit) : (uint32_t)kRadix;
     dig[r] = d;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned peers = digit_peers(d);
     const int leader = __ffs(peers) - 1;
     uint32_t basev = 0;
     if (lane == leader && valid) {
@@ -324,30 +323,77 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     __syncwarp();
   }
   __syncthreads();
-  // per-digit exclusive offsets across warps, then across digits
-  {
-    const int d = threadIdx.x;
-    uint32_t run = 0;
+  const int d = threadIdx.x;  // thread d looks after digit d from here on
+  const uint64_t tag = (uint64_t)pass_tag << 56;
+  uint64_t *mine = look + (uint64_t)t * kRadix + d;
+  uint32_t run = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const uint32_t c = wcount[w * kRadix + d];
-      wcount[w * kRadix + d] = run;
-      run += c;
-    }
-    const uint32_t ex = block_exclusive_scan(run, nullptr);
-    dstart[d] = ex;
+  for (int w = 0; w < 8; ++w) {
+    const uint32_t c = wcount[w * kRadix + d];
+    wcount[w * kRadix + d] = run;
+    run += c;
   }
-  __syncthreads();
+  // the tile's own count goes out first, so that later tiles can pass it
+  st_relaxed_u64(mine, (t == 0 ? kLookTotal : kLookOwn) | tag | run);
+  dstart[d] = block_exclusive_scan(run);
+  const uint32_t digit_base = block_exclusive_scan(hist[d]);
+  // the tile in sorted order in shared memory (slots inside the tile only)
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
-    const uint32_t d = dig[r];
-    if (d < kRadix) {
-      const uint32_t pos = dstart[d] + wcount[warp * kRadix + d] + rank[r];
+    const uint32_t dd = dig[r];
+    if (dd < kRadix) {
+      const uint32_t pos = dstart[dd] + wcount[warp * kRadix + dd] + rank[r];
 #pragma unroll
       for (int w = 0; w < KW; ++w) sk[(size_t)pos * KW + w] = k[r][w];
       sv[pos] = v[r];
     }
   }
+  // look back over the preceding tiles, kLookWindow words per round trip:
+  // own counts are summed until a running total ends the walk
+  uint32_t before = 0;
+  if (t > 0) {
+    int64_t j = (int64_t)t - 1;
+    bool done = false;
+    uint32_t idle = 0;
+    uint64_t t0 = 0;
+    while (!done) {
+      uint64_t wv[kLookWindow];
+#pragma unroll
+      for (int i = 0; i < kLookWindow; ++i)
+        wv[i] = j - i >= 0 ? ld_relaxed_u64(look + (uint64_t)(j - i) * kRadix + d) : 0ull;
+      int used = 0;
+      bool gap = false;
+#pragma unroll
+      for (int i = 0; i < kLookWindow; ++i) {
+        if (done || gap) continue;
+        const uint64_t x = wv[i];
+        if (j - i < 0) {
+          done = true;  // past tile 0, which always holds a total
+        } else if ((x >> 62) != 0 && ((x >> 56) & 0x3Fu) == pass_tag) {
+          before += (uint32_t)x;
+          ++used;
+          done = (x >> 62) == 2;
+        } else {
+          gap = true;   // not published yet
+        }
+      }
+      j -= used;
+      if (!done && used == 0) {
+        __nanosleep(64);
+        if ((++idle & 15u) == 0) {
+          const uint64_t now = sort_clock_ns();
+          if (t0 == 0) {
+            t0 = now;
+          } else if (now - t0 > kLookLimitNs) {
+            atomicOr(status, kStatusTimeout);
+            break;
+          }
+        }
+      }
+    }
+    st_relaxed_u64(mine, kLookTotal | tag | (uint32_t)(before + run));
+  }
+  gbase[d] = digit_base + before;
   __syncthreads();
   const uint64_t rem = nnz - tile_base;
   const uint32_t count = rem < (uint64_t)kSortTile ? (uint32_t)rem : (uint32_t)kSortTile;
@@ -358,12 +404,14 @@ __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
       uint64_t kk[KW];
 #pragma unroll
       for (int w = 0; w < KW; ++w) kk[w] = sk[(size_t)idx * KW + w];
-      const uint64_t kd = (KW == 2 && word) ? kk[KW - 1] : kk[0];
-      const uint32_t d = (uint32_t)((kd >> shift) & 0xFFu);
+      const uint32_t d = sort_digit<KW>(kk, bit);
       const uint64_t dst = (uint64_t)gbase[d] + (idx - dstart[d]);
+      // a timed-out look-back leaves wrong offsets: stay inside the arrays
+      if (dst < nnz) {
 #pragma unroll
-      for (int w = 0; w < KW; ++w) keys_out[dst * KW + w] = kk[w];
-      vals_out[dst] = sv[idx];
+        for (int w = 0; w < KW; ++w) keys_out[dst * KW + w] = kk[w];
+        vals_out[dst] = sv[idx];
+      }
     }
   }
 }
@@ -594,74 +642,91 @@ cudaError_t launch_norm(int kw, const uint64_t *keys, const float *vals, uint64_
   return cudaGetLastError();
 }
 
-size_t sort_table_entries(uint64_t nnz) {
+size_t sort_workspace_bytes(uint64_t nnz) {
   const uint64_t ntiles = (nnz + kSortTile - 1) / kSortTile;
-  return (size_t)ntiles * kRadix;
+  return (size_t)ntiles * kRadix * 8 + (size_t)kMaxSortPasses * kRadix * 4 + kMaxSortPasses * 4;
 }
 
-size_t sort_scan_blocks(uint64_t nnz) {
-  return (sort_table_entries(nnz) + kScanBlock - 1) / kScanBlock;
-}
-
-static size_t downsweep_smem(int kw) {
+static size_t pass_smem(int kw) {
   return (size_t)kSortTile * (8 * kw + 4) + (8 * kRadix + 2 * kRadix) * 4;
 }
 
-cudaError_t launch_radix_sort(int kw, int nbits, uint64_t nnz, uint64_t *keys[2], float *vals[2],
-                              const float *vals_in, uint32_t *table, uint32_t *table_scan,
-                              uint32_t *block_sums, int *final_buf, cudaStream_t s) {
-  // keys[0] holds the input positions; vals_in the input values. The result
-  // ends in keys[*final_buf] / vals[*final_buf].
-  *final_buf = 0;
-  if (nnz == 0) return cudaSuccess;
-  const int passes = (nbits + 7) / 8;
-  if (passes == 0) {
-    cudaError_t e = cudaMemcpyAsync(vals[0], vals_in, nnz * sizeof(float),
-                                    cudaMemcpyDeviceToDevice, s);
-    return e;
+template <int KW>
+static cudaError_t radix_sort_t(int passes, uint64_t nnz, uint64_t *keys[2], float *vals[2],
+                                const float *vals_in, void *work, uint32_t *status,
+                                bool skip_constant, int *final_buf, int *passes_run, int num_sms,
+                                cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(radix_pass_kernel<KW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pass_smem(KW));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
   }
   const uint32_t ntiles = (uint32_t)((nnz + kSortTile - 1) / kSortTile);
-  const uint64_t entries = (uint64_t)ntiles * kRadix;
-  const uint32_t nblocks = (uint32_t)((entries + kScanBlock - 1) / kScanBlock);
-  const size_t smem = downsweep_smem(kw);
-  static bool attr_set[3] = {false, false, false};
-  if (!attr_set[kw]) {
-    cudaError_t e = kw == 1 ? cudaFuncSetAttribute(radix_downsweep<1>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)downsweep_smem(1))
-                            : cudaFuncSetAttribute(radix_downsweep<2>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)downsweep_smem(2));
-    if (e != cudaSuccess) return e;
-    attr_set[kw] = true;
+  uint64_t *look = static_cast<uint64_t *>(work);
+  uint32_t *hist = reinterpret_cast<uint32_t *>(look + (size_t)ntiles * kRadix);
+  uint32_t *tickets = hist + kMaxSortPasses * kRadix;
+  cudaError_t e = cudaMemsetAsync(work, 0, sort_workspace_bytes(nnz), s);
+  if (e != cudaSuccess) return e;
+  const uint64_t per_block = (uint64_t)kSortThreads * kHistItems;
+  const uint64_t hist_blocks = (nnz + per_block - 1) / per_block;
+  const int hgrid = (int)std::min<uint64_t>(hist_blocks, (uint64_t)num_sms * 4);
+  radix_hist_kernel<KW><<<hgrid, kSortThreads, 0, s>>>(keys[0], nnz, passes, hist);
+  note_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  bool skip[kMaxSortPasses] = {};
+  if (skip_constant) {
+    // a digit that one value covers leaves the order as it is
+    std::vector<uint32_t> hh((size_t)passes * kRadix);
+    if ((e = cudaMemcpyAsync(hh.data(), hist, hh.size() * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return e;
+    for (int p = 0; p < passes; ++p)
+      for (int d = 0; d < kRadix; ++d)
+        if (hh[(size_t)p * kRadix + d] == nnz) skip[p] = true;
   }
   int cur = 0;
   const float *vin = vals_in;
   for (int p = 0; p < passes; ++p) {
-    const int bit = p * 8;
-    const int word = bit >> 6, shift = bit & 63;
-    if (kw == 1)
-      radix_upsweep<1><<<ntiles, kSortThreads, 0, s>>>(keys[cur], nnz, word, shift, ntiles, table);
-    else
-      radix_upsweep<2><<<ntiles, kSortThreads, 0, s>>>(keys[cur], nnz, word, shift, ntiles, table);
-    scan_reduce<<<nblocks, kScanThreads, 0, s>>>(table, entries, block_sums);
-    scan_top<<<1, kScanThreads, 0, s>>>(block_sums, nblocks);
-    scan_down<<<nblocks, kScanThreads, 0, s>>>(table, entries, block_sums, table_scan);
+    if (skip[p]) continue;
     const int nxt = cur ^ 1;
-    if (kw == 1)
-      radix_downsweep<1><<<ntiles, kSortThreads, smem, s>>>(keys[cur], vin, nnz, word, shift, ntiles,
-                                                            table_scan, keys[nxt], vals[nxt]);
-    else
-      radix_downsweep<2><<<ntiles, kSortThreads, smem, s>>>(keys[cur], vin, nnz, word, shift, ntiles,
-                                                            table_scan, keys[nxt], vals[nxt]);
-    note_launches(5);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    radix_pass_kernel<KW><<<ntiles, kSortThreads, pass_smem(KW), s>>>(
+        keys[cur], vin, nnz, 8 * p, (uint32_t)(p + 1), hist + (size_t)p * kRadix, look, tickets + p,
+        status, keys[nxt], vals[nxt]);
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     cur = nxt;
     vin = vals[cur];
+    if (passes_run) ++*passes_run;
+  }
+  if (vin == vals_in) {
+    // no pass moved anything: the values are still the caller's
+    if ((e = cudaMemcpyAsync(vals[0], vals_in, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+      return e;
   }
   *final_buf = cur;
   return cudaSuccess;
+}
+
+cudaError_t launch_radix_sort(int kw, int nbits, uint64_t nnz, uint64_t *keys[2], float *vals[2],
+                              const float *vals_in, void *work, uint32_t *status, bool skip_constant,
+                              int *final_buf, int *passes_run, int num_sms, cudaStream_t s) {
+  // keys[0] holds the input positions; vals_in the input values. The result
+  // ends in keys[*final_buf] / vals[*final_buf].
+  *final_buf = 0;
+  if (passes_run) *passes_run = 0;
+  if (nnz == 0) return cudaSuccess;
+  const int passes = (nbits + 7) / 8;
+  if (passes == 0)
+    return cudaMemcpyAsync(vals[0], vals_in, nnz * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (kw == 1)
+    return radix_sort_t<1>(passes, nnz, keys, vals, vals_in, work, status, skip_constant, final_buf,
+                           passes_run, num_sms, s);
+  return radix_sort_t<2>(passes, nnz, keys, vals, vals_in, work, status, skip_constant, final_buf,
+                         passes_run, num_sms, s);
 }
 
 cudaError_t launch_partition(const DecodePlan &dp, const uint64_t *keys, uint64_t nnz, uint64_t L,

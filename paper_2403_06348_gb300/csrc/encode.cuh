@@ -14,12 +14,19 @@ uint64_t norm_chunks(uint64_t nnz);
 cudaError_t launch_norm(int kw, const uint64_t *keys, const float *vals, uint64_t nnz, double *head,
                         double *tail, uint8_t *flags, double *norm_sq, int num_sms, cudaStream_t s);
 
-size_t sort_table_entries(uint64_t nnz);
-size_t sort_scan_blocks(uint64_t nnz);
+// Device workspace of launch_radix_sort (look-back words, digit counts, tickets).
+size_t sort_workspace_bytes(uint64_t nnz);
 
+// Stable LSD radix sort of nnz (position, value) pairs on their low nbits
+// bits. keys[0] holds the positions, vals_in the values; the result lands in
+// keys[*final_buf] / vals[*final_buf]. work holds sort_workspace_bytes(nnz)
+// bytes. A bounded look-back wait that expires sets kStatusTimeout in *status.
+// skip_constant reads the digit counts back (one stream synchronisation) and
+// leaves out every pass whose digit is the same for all positions.
+// *passes_run (may be NULL) counts the passes launched.
 cudaError_t launch_radix_sort(int kw, int nbits, uint64_t nnz, uint64_t *keys[2], float *vals[2],
-                              const float *vals_in, uint32_t *table, uint32_t *table_scan,
-                              uint32_t *block_sums, int *final_buf, cudaStream_t s);
+                              const float *vals_in, void *work, uint32_t *status, bool skip_constant,
+                              int *final_buf, int *passes_run, int num_sms, cudaStream_t s);
 
 cudaError_t launch_partition(const DecodePlan &dp, const uint64_t *keys, uint64_t nnz, uint64_t L,
                              uint32_t *intervals, uint32_t *max_len, int num_sms, cudaStream_t s);

@@ -151,5 +151,8 @@ struct alto_tensor {
   std::vector<ProfEvt> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[ALTO_PROF_KINDS] = {};
+  float encode_ms = 0.f;  // device time of the encode kernels (CUDA events)
+  float sort_ms = 0.f;    // of which the radix sort
+  int sort_passes = 0;    // radix passes the sort launched
   uint64_t prof_n[ALTO_PROF_KINDS] = {};
 };

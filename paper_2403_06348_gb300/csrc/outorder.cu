@@ -228,18 +228,16 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
   const int nbits = bit_width_u64(L - 1) + bits;  // <= 32 + 32
   uint64_t *kbuf[2] = {nullptr, nullptr};
   float *vbuf[2] = {nullptr, nullptr};
-  uint32_t *pos = nullptr, *table = nullptr, *table_scan = nullptr, *block_sums = nullptr;
-  const size_t entries = sort_table_entries(M);
-  const size_t nblocks = std::max<size_t>(sort_scan_blocks(M), 1);
+  uint32_t *pos = nullptr;
+  void *sort_work = nullptr;
+  const size_t sort_bytes = sort_workspace_bytes(M);
   auto release = [&](int keep) {
     for (int b = 0; b < 2; ++b) {
       dfree(h, kbuf[b], M * 8, s);
       if (b != keep) dfree(h, vbuf[b], M * 4, s);
     }
     dfree(h, pos, M * 4, s);
-    dfree(h, table, entries * 4, s);
-    dfree(h, table_scan, entries * 4, s);
-    dfree(h, block_sums, nblocks * 4, s);
+    dfree(h, sort_work, sort_bytes, s);
   };
   uint32_t *res = static_cast<uint32_t *>(dalloc(h, std::max<uint64_t>(M, 1) * 4, s));
   if (!res) return fail(ALTO_ERR_OOM, "pos_out of %llu entries", (unsigned long long)M);
@@ -283,10 +281,8 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
     vbuf[b] = b == 0 ? reinterpret_cast<float *>(res) : static_cast<float *>(dalloc(h, M * 4, s));
   }
   pos = static_cast<uint32_t *>(dalloc(h, M * 4, s));
-  table = static_cast<uint32_t *>(dalloc(h, entries * 4, s));
-  table_scan = static_cast<uint32_t *>(dalloc(h, entries * 4, s));
-  block_sums = static_cast<uint32_t *>(dalloc(h, nblocks * 4, s));
-  if (!kbuf[0] || !kbuf[1] || !vbuf[1] || !pos || !table || !table_scan || !block_sums) {
+  sort_work = dalloc(h, sort_bytes, s);
+  if (!kbuf[0] || !kbuf[1] || !vbuf[1] || !pos || !sort_work) {
     release(-1);
     return fail(ALTO_ERR_OOM, "pos_out sort scratch for %llu entries", (unsigned long long)M);
   }
@@ -301,8 +297,8 @@ alto_status build_pos_out(alto_tensor *h, int mode, uint64_t L, uint32_t **out, 
   int fbuf = 0;
   // the positions travel through the sort as 32-bit payload words, bit for bit
   if (e == cudaSuccess)
-    e = launch_radix_sort(1, nbits, M, kbuf, vbuf, reinterpret_cast<const float *>(pos), table,
-                          table_scan, block_sums, &fbuf, s);
+    e = launch_radix_sort(1, nbits, M, kbuf, vbuf, reinterpret_cast<const float *>(pos), sort_work,
+                          h->status_dev, false, &fbuf, nullptr, h->num_sms, s);
   if (e != cudaSuccess) {
     release(-1);
     return fail(ALTO_ERR_CUDA, "pos_out: %s", cudaGetErrorString(e));

@@ -145,3 +145,58 @@ def test_device_inputs_of_the_wrong_dtype_are_refused():
     t = alto.alto_encode(c.to(torch.int32), v, (4, 4, 4))
     assert t.nnz == 10
     t.free()
+
+
+def _launched_passes(ref, nbits):
+    """8-bit digits of the sort that are not the same for every nonzero: the
+    passes the sort must launch (a constant digit leaves the order as it is)."""
+    n = 0
+    for p in range((nbits + 7) // 8):
+        word, shift = divmod(8 * p, 64)
+        k = ref.lo if word == 0 else ref.hi
+        if len(np.unique((k >> np.uint64(shift)) & np.uint64(0xFF))) > 1:
+            n += 1
+    return n
+
+
+@pytest.mark.parametrize("dims,limit,M,seed", [
+    ((1 << 20,) * 3, 16, 50_000, 21),      # 60 bits, only the low 12 vary
+    ((1 << 20,) * 5, 1024, 30_000, 22),    # 100 bits (two words), the high word constant
+    ((1 << 22, 3, 1 << 18), 1 << 18, 20_000, 23),  # every digit varies
+])
+def test_constant_digits_are_skipped(dims, limit, M, seed):
+    rng = np.random.default_rng(seed)
+    coords = np.stack([rng.integers(0, min(d, limit), M) for d in dims]).astype(np.uint32)
+    vals = (1.0 - rng.random(M)).astype(np.float32)
+    t, ref = _check(coords, vals, dims)
+    info = t.query()
+    assert info.sort_passes == _launched_passes(ref, ref.plan.nbits)
+    assert info.sort_passes < (ref.plan.nbits + 7) // 8 or limit >= 1 << 18
+    assert info.encode_ms > 0 and 0 < info.sort_ms <= info.encode_ms
+
+
+def test_every_digit_constant():
+    """All nonzeros at one position: no pass runs, the values keep input order."""
+    M = 9000
+    coords = np.tile(np.array([[5], [700], [3]], np.uint32), (1, M))
+    vals = np.arange(M, dtype=np.float32)
+    t, _ = _check(coords, vals, (10, 1000, 4))
+    assert t.query().sort_passes == 0
+
+
+@pytest.mark.parametrize("M", [4095, 4096, 4097, 2 * 4096 + 1, 61 * 4096 - 7])
+def test_sort_tile_edges(M):
+    coords, vals = gu.rand_tensor((5000, 3000, 2000), M, M)
+    _check(coords, vals, (5000, 3000, 2000))
+
+
+@pytest.mark.parametrize("dims", [(1000, 800, 600), (1 << 20,) * 5])
+def test_duplicates_across_passes_keep_input_order(dims):
+    """500 distinct positions spread over every digit, drawn 200k times: equal
+    positions must come out in input order through every pass and tile."""
+    rng = np.random.default_rng(31)
+    pool = np.stack([rng.integers(0, d, 500) for d in dims]).astype(np.uint32)
+    pick = rng.integers(0, 500, 200_000)
+    coords = np.ascontiguousarray(pool[:, pick])
+    vals = np.arange(200_000, dtype=np.float32)
+    _check(coords, vals, dims, L=11)
