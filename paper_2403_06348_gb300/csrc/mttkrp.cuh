@@ -50,9 +50,9 @@ struct MttkrpArgs {
   const uint32_t *perm;
   // in-tile output-oriented traversal (TILED): htab holds nbins hot rows, the
   // first nslots of them staged in shared memory, the rest ("warm") summed in
-  // kWarmReps replicas [kWarmReps][nbins][R] (zero between launches)
+  // kWarmReps fp64 replicas [kWarmReps][nbins][R] (zero between launches)
   int nbins;
-  float *warm;
+  double *warm;
   uint32_t *status;            // device status word (kStatusTimeout)
   // byte-table decode (one-word positions): the table [8][256] in global
   // memory, copied into shared memory by the kernels that use it; null: none
@@ -124,7 +124,7 @@ size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits
 
 // out(row of warm slot i, :) = sum of the kWarmReps replicas of slot i, for
 // slots nslots..nbins-1; the replicas are zeroed again for the next launch.
-cudaError_t launch_warm_reduce(float *warm, const uint32_t *slot_rows, int nslots, int nbins, int R,
+cudaError_t launch_warm_reduce(double *warm, const uint32_t *slot_rows, int nslots, int nbins, int R,
                                float *out, int num_sms, cudaStream_t s);
 
 // Replicas of the warm rows used by the TILED kernel.

@@ -23,13 +23,14 @@
 //     carries the run of equal output rows in registers.
 //  5. A run leaves when its row changes: staged hot rows (the first nslots)
 //     into shared memory, flushed once per CTA at the end; the remaining hot
-//     rows ("warm") into one of kWarmReps fp32 replicas (vector atomics; a
-//     small kernel adds the replicas into the output afterwards), which keeps
-//     every fp32 accumulation chain short; all other rows straight into the
-//     output (red.global.add.v4.f32).
+//     rows ("warm") into one of kWarmReps fp64 replicas (fp64 atomics; a
+//     small kernel adds the replicas into the output afterwards): a warm row
+//     takes an addition from every tile that holds it, too long a chain for
+//     fp32; all other rows straight into the output (red.global.add.v4.f32).
 #pragma once
 
 #include "mttkrp_kernel.cuh"
+#include "async_copy.cuh"
 
 namespace alto {
 
@@ -77,66 +78,6 @@ __host__ __device__ inline TileLayout tile_layout(int kw, int rec_bytes, int ngr
   L.lut = L.bar + 16;
   L.total = L.lut + (lut ? (uint32_t)kLutBytes : 0u);
   return L;
-}
-
-// ---------------------------------------------------------------------------
-// mbarrier / bulk-copy helpers (inline PTX)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple
-// of 16), completion counted on bar.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits for phase `parity` of bar to complete, giving up after limit_ns.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
-  }
 }
 
 constexpr uint64_t kTileWaitNs = 2000000000ull;  // 2 s: a tile copy takes microseconds
@@ -219,10 +160,11 @@ __device__ __forceinline__ void tile_flush(const uint64_t (&run)[CPL / 2], uint3
       flush_run<CPL>(f, 0u, idx, stage, a.out, a.R, sub, tpn, grp);
       return;
     }
-    float *w = a.warm + ((size_t)(blockIdx.x % kWarmReps) * (size_t)a.nbins + (size_t)idx) * (size_t)a.R;
+    // fp64: a warm row takes one addition per tile that holds it, tens of
+    // thousands on a Zipf head, too long a chain for fp32
+    double *w = a.warm + ((size_t)(blockIdx.x % kWarmReps) * (size_t)a.nbins + (size_t)idx) * (size_t)a.R;
 #pragma unroll
-    for (int v = 0; v < CPL / 4; ++v)
-      red_v4(w + CPL * sub + 4 * v, f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+    for (int c = 0; c < CPL; ++c) atomicAdd(w + CPL * sub + c, (double)f[c]);
     return;
   }
   float *o = a.out + (uint64_t)code * (uint64_t)a.R;

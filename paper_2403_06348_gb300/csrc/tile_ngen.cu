@@ -22,35 +22,34 @@ size_t tile_smem_bytes(int nmodes, int kw, int R, int cpl, int nslots, int hbits
   return tile_layout(kw, rw * 4, kTileThreads / (R / cpl), R, nslots, hbits, nbins, lut).total;
 }
 
-// One thread per 4 columns of a warm slot: the replicas summed in slot
-// order, the row written (every update of a warm row went to the replicas),
-// the replicas cleared.
-__global__ void __launch_bounds__(256) warm_reduce_kernel(float *__restrict__ warm,
+// One thread per 2 columns of a warm slot: the fp64 replicas summed in slot
+// order, the row written in fp32 (every update of a warm row went to the
+// replicas), the replicas cleared.
+__global__ void __launch_bounds__(256) warm_reduce_kernel(double *__restrict__ warm,
                                                           const uint32_t *__restrict__ slot_rows,
                                                           int nslots, int nbins, int R,
                                                           float *__restrict__ out) {
-  const int per_row = R / 4;
+  const int per_row = R / 2;
   const int total = (nbins - nslots) * per_row;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int slot = nslots + i / per_row, c4 = (i % per_row) * 4;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int slot = nslots + i / per_row, c2 = (i % per_row) * 2;
+    double2 acc = make_double2(0.0, 0.0);
 #pragma unroll 4
     for (int g = 0; g < kWarmReps; ++g) {
-      float4 *p = reinterpret_cast<float4 *>(warm + ((size_t)g * nbins + slot) * R + c4);
-      const float4 v = *p;
+      double2 *p = reinterpret_cast<double2 *>(warm + ((size_t)g * nbins + slot) * R + c2);
+      const double2 v = *p;
       acc.x += v.x;
       acc.y += v.y;
-      acc.z += v.z;
-      acc.w += v.w;
-      *p = make_float4(0.f, 0.f, 0.f, 0.f);
+      *p = make_double2(0.0, 0.0);
     }
-    *reinterpret_cast<float4 *>(out + (uint64_t)slot_rows[slot] * R + c4) = acc;
+    *reinterpret_cast<float2 *>(out + (uint64_t)slot_rows[slot] * R + c2) =
+        make_float2((float)acc.x, (float)acc.y);
   }
 }
 
-cudaError_t launch_warm_reduce(float *warm, const uint32_t *slot_rows, int nslots, int nbins, int R,
+cudaError_t launch_warm_reduce(double *warm, const uint32_t *slot_rows, int nslots, int nbins, int R,
                                float *out, int num_sms, cudaStream_t s) {
-  const int total = (nbins - nslots) * (R / 4);
+  const int total = (nbins - nslots) * (R / 2);
   if (total <= 0) return cudaSuccess;
   int grid = (total + 255) / 256;
   if (grid > num_sms * 4) grid = num_sms * 4;
