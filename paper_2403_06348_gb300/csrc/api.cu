@@ -724,7 +724,7 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
       a.lp = h->lut_plan;
     }
     if (a.nbins > a.nslots) {
-      const size_t need = (size_t)kTileWarmReps * (size_t)a.nbins * (size_t)R * sizeof(float);
+      const size_t need = (size_t)kTileWarmReps * (size_t)a.nbins * (size_t)R * sizeof(double);
       if (h->warm.bytes < need) {
         dfree(h, h->warm.p, h->warm.bytes, s);
         h->warm.p = dalloc(h, need, s);
@@ -733,7 +733,7 @@ alto_status mttkrp_impl(alto_tensor *h, int mode, const void *const *factors, bo
         // zero once; every launch leaves the replicas zero again
         CUDA_TRY(cudaMemsetAsync(h->warm.p, 0, need, s));
       }
-      a.warm = static_cast<float *>(h->warm.p);
+      a.warm = static_cast<double *>(h->warm.p);
     }
     {
       ProfScope ps(h, ALTO_PROF_ZERO, s);
@@ -1392,7 +1392,7 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
   };
   const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_s = take((size_t)N * R * 8),
                o_Sn = take((size_t)R * 8), o_BtB = take(RR * 8), o_dot = take((size_t)R * 8),
-               o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
+               o_W = take(2 * RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
                o_wcol = take((size_t)R * 8), o_rscale = take((size_t)R * 8),
                o_int = take(16), o_fac = take(host_factors ? sumI * R * 4 : 0);
   char *ws = static_cast<char *>(dalloc(h, off, s));
@@ -1481,7 +1481,11 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
       CP_TRY(cudaMemsetAsync(dot, 0, (size_t)R * 8, s));
       {
         ProfScope ps(h, ALTO_PROF_RMUL, s);
-        CP_TRY(launch_update(Mbuf, W, A[n], h->dims[n], R, BtB, dot, done_at, it, h->num_sms, s));
+        if (update_tc_supported(R))
+          CP_TRY(launch_update_tc(Mbuf, W, A[n], h->dims[n], R, BtB, dot, done_at, it, h->status_dev,
+                                  h->num_sms, s));
+        else
+          CP_TRY(launch_update(Mbuf, W, A[n], h->dims[n], R, BtB, dot, done_at, it, h->num_sms, s));
       }
       {
         ProfScope ps(h, ALTO_PROF_SOLVE, s);
@@ -1518,6 +1522,7 @@ alto_status cpals_run(alto_handle_t h, int R, int iters, float *const *factors, 
     cudaStreamSynchronize(s);
     return finish(fail(ALTO_ERR_NOT_SPD, "V of Alg. 1 is not positive definite"));
   }
+  if (status & kStatusTimeout) return finish(fail(ALTO_ERR_TIMEOUT, "CP-ALS: a bounded wait expired"));
   return finish(ALTO_OK);
 }
 

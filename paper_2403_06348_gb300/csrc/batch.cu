@@ -661,7 +661,7 @@ alto_status alto_batch_add(alto_batch_t b, alto_handle_t h, int R, int iters, do
   };
   const size_t o_M = take(maxI * R * 4), o_G = take(N * RR * 8), o_s = take((size_t)N * R * 8),
                o_Sn = take((size_t)R * 8), o_BtB = take(RR * 8), o_dot = take((size_t)R * 8),
-               o_W = take(RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
+               o_W = take(2 * RR * 4), o_fits = take((size_t)iters * 8), o_lam = take((size_t)R * 8),
                o_wcol = take((size_t)R * 8), o_rscale = take((size_t)R * 8);
   size_t o_B[kMaxModes];
   for (int m = 0; m < N; ++m) o_B[m] = take(h->dims[m] * R * 4);
@@ -894,7 +894,7 @@ alto_status alto_cpals_footprint(int nmodes, const uint64_t *dims, uint64_t nnz,
   const uint64_t L = std::max<uint64_t>(1, (nnz + kBatchSegNnz - 1) / kBatchSegNnz);
   const uint64_t tensor = nnz * (8 * kw + 4) + L * nmodes * 8 + 4096;
   const uint64_t RR = (uint64_t)R * R;
-  const uint64_t run = maxI * R * 4 + nmodes * RR * 8 + nmodes * (uint64_t)R * 8 + RR * 20 +
+  const uint64_t run = maxI * R * 4 + nmodes * RR * 8 + nmodes * (uint64_t)R * 8 + RR * 24 +
                        (uint64_t)R * 40 + (uint64_t)iters * 8 + sumI * R * 4 + 4096;
   // encode: the coordinates, the positions and values twice (sort buffers)
   const uint64_t encode = nnz * (4ull * nmodes + 2 * (8 * kw + 4));

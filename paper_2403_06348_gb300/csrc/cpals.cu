@@ -2,11 +2,13 @@
 //
 // Per mode n (factors stored as B_m with A_m = B_m diag(s_m)):
 //   prepare_kernel  one CTA, fp64: V = Hadamard product of the other Grams,
-//                   Cholesky V = L L^T, V^-1, Sn = prod_{m != n} s_m and
-//                   W = diag(Sn) V^-1. MTTKRP over the stored B's gives
-//                   M_B = M diag(1/Sn), so M V^-1 = M_B W.
+//                   Cholesky V = L L^T, X = L^-1, Sn = prod_{m != n} s_m and
+//                   the solve factors W1 = diag(Sn) X^T, W2 = X (V^-1 =
+//                   X^T X is never formed). MTTKRP over the stored B's gives
+//                   M_B = M diag(1/Sn), so M V^-1 = (M_B W1) W2.
 //   (MTTKRP)
-//   update_kernel   B_n = M_B W in one pass over M_B, accumulating B_n^T B_n
+//   update_kernel   B_n = (M_B W1) W2 in one pass over M_B (update_tc_kernel
+//                   on the tensor cores for R = 16, 32), accumulating B_n^T B_n
 //                   and sum_i M_B(i,r) B_n(i,r) (fp32 partial sums over at most
 //                   1024 rows, fp64 combine).
 //   finish_kernel   one CTA, fp64: lambda_r = ||B_n(:,r)||, s_n = 1/lambda
@@ -86,14 +88,15 @@ __global__ void __launch_bounds__(256) prepare_kernel(const CpArgs a) {
   prepare_body(a, sd);
 }
 
-// B_n = M_B W with B_n^T B_n and the column dot products
+// B_n = (M_B W1) W2 with B_n^T B_n and the column dot products
 // sum_i M_B(i,r) B_n(i,r) in the same pass over M_B (the solve step of Alg. 1
 // and the Gram and fit terms it needs, formed from the B_n values that are
 // stored).
 //
 // A tile is TR = 4096 / R rows (16 KB), loaded into registers one tile ahead
 // and stored transposed in shared memory. Thread (rb, cb) computes the 4 x 4
-// block of B_n at rows 4 rb.., columns 4 cb.. (R steps of 16 FMA) and its
+// block of Y = M_B W1 at rows 4 rb.., columns 4 cb.. (R steps of 16 FMA),
+// puts it in shared memory, computes its block of B_n = Y W2 the same way and
 // part of the dot products; the block also goes to shared memory, from which
 // every thread then accumulates one 4 x 4 block (bi <= bj) of B_n^T B_n over a
 // share of the tile's rows (the blocks on and above the diagonal spread over
@@ -118,9 +121,10 @@ __global__ void __launch_bounds__(kUgThreads, ALTO_UG_MIN_BLOCKS)
   extern __shared__ __align__(16) unsigned char smraw[];
   double *slot = reinterpret_cast<double *>(smraw);           // [kUgThreads][16]
   double *dsum = slot + kUgThreads * 16;                       // [R]
-  float *w = reinterpret_cast<float *>(dsum + R);              // R * R
-  float *mt = w + R * R;                                       // R * TRP (M tile, column-major)
-  float *bt = mt + R * TRP;                                    // TR * RP (B tile, row-major)
+  float *w = reinterpret_cast<float *>(dsum + R);              // 2 R * R: W1, W2
+  float *mt = w + 2 * R * R;                                   // R * TRP (M tile, column-major)
+  float *bt = mt + R * TRP;                                    // TR * RP (B tile, row-major;
+                                                               // first M W1, column-major)
   const int tid = threadIdx.x;
   const int cb = tid % B4, rb = tid / B4;
   // Gram block of this thread: block b = tid mod BB of the upper triangle,
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kUgThreads, ALTO_UG_MIN_BLOCKS)
     ++bi;
   }
   const int bj = bi + rem;
-  for (int i = tid; i < R * R; i += kUgThreads) w[i] = W[i];
+  for (int i = tid; i < 2 * R * R; i += kUgThreads) w[i] = W[i];
   for (int i = tid; i < R; i += kUgThreads) dsum[i] = 0.0;
 #pragma unroll
   for (int i = 0; i < 16; ++i) slot[tid * 16 + i] = 0.0;
@@ -185,22 +189,16 @@ __global__ void __launch_bounds__(kUgThreads, ALTO_UG_MIN_BLOCKS)
     }
     if (t + gridDim.x < ntiles) load_tile(t + gridDim.x);
     __syncthreads();
-    // B_n block: rows 4 rb .. 4 rb + 3, columns 4 cb .. 4 cb + 3
+    // B_n block: rows 4 rb .. 4 rb + 3, columns 4 cb .. 4 cb + 3, as
+    // (M W1) W2 with the block of M W1 passing through shared memory
     float o[4][4];
+    block_product(mt, TRP, w, R, rb, cb, o);
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
-#pragma unroll 8
-    for (int k = 0; k < R; ++k) {
-      const float4 mk = *reinterpret_cast<const float4 *>(mt + k * TRP + 4 * rb);
-      const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + 4 * cb);
-      const float ma[4] = {mk.x, mk.y, mk.z, mk.w}, wa[4] = {wk.x, wk.y, wk.z, wk.w};
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) o[x][y] = fmaf(ma[x], wa[y], o[x][y]);
-    }
+    for (int y = 0; y < 4; ++y)
+      *reinterpret_cast<float4 *>(bt + (4 * cb + y) * TRP + 4 * rb) = make_float4(o[0][y], o[1][y], o[2][y], o[3][y]);
+    __syncthreads();
+    block_product(bt, TRP, w + R * R, R, rb, cb, o);
+    __syncthreads();  // every read of M W1 is done before B overwrites it
     // dot products with M_B (rows past nrows are 0 in both)
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
@@ -252,7 +250,7 @@ __global__ void __launch_bounds__(kUgThreads, ALTO_UG_MIN_BLOCKS)
 template <int R>
 constexpr size_t update_smem_r() {
   return (size_t)(kUgThreads * 16 + R) * sizeof(double) +
-         (size_t)(R * R + R * (4096 / R + 4) + (4096 / R) * (R + 4)) * sizeof(float);
+         (size_t)(2 * R * R + R * (4096 / R + 4) + (4096 / R) * (R + 4)) * sizeof(float);
 }
 
 __global__ void __launch_bounds__(256) finish_kernel(const CpArgs a) { finish_body(a); }

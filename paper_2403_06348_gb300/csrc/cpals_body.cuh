@@ -13,16 +13,18 @@ constexpr int kUpdThreads = 256;
 inline size_t update_smem(int R) {
   const int TR = 4096 / R;
   return (size_t)(R * R + R) * sizeof(double) +
-         (size_t)(R * R + R * (TR + 4) + TR * (R + 4)) * sizeof(float);
+         (size_t)(2 * R * R + R * (TR + 4) + TR * (R + 4)) * sizeof(float);
 }
 
 // Pseudo-inverse of the symmetric R x R matrix A (destroyed) into Y, with Q
 // as work space: cyclic Jacobi rotations in the round-robin order (R/2
 // disjoint pairs per step, R - 1 steps per sweep; Golub and Van Loan,
 // "parallel Jacobi") until the off-diagonal mass is below 1e-15 of the
-// total, then Y = Q diag(1/lambda) Q^T over the eigenvalues with |lambda| >
-// 1e-15 max |lambda| (the cut numpy's pinv makes). Returns false if A has a
-// non-finite entry. Called by all threads of the CTA.
+// total. Then A^+ = Q diag(1/lambda) Q^T over the eigenvalues with |lambda| >
+// 1e-15 max |lambda| (the cut numpy's pinv makes) leaves as two factors,
+// A^+ = F G: F = Q |Lambda|^-1/2 into Y and G = sign(Lambda) |Lambda|^-1/2 Q^T
+// into A (columns of F and rows of G under the cut are 0). Returns false if
+// A has a non-finite entry. Called by all threads of the CTA.
 __device__ __forceinline__ bool pinv_body(double *A, double *Q, double *Y, int R, int lgR) {
   const int tid = threadIdx.x, nt = blockDim.x, RR = R * R, half = R / 2;
   __shared__ double c_s[ALTO_MAX_RANK / 2], s_s[ALTO_MAX_RANK / 2], red[2][32];
@@ -105,24 +107,26 @@ __device__ __forceinline__ bool pinv_body(double *A, double *Q, double *Y, int R
     }
   }
   // eigenvalues on the diagonal; the cut relative to the largest
+  __shared__ double ev[ALTO_MAX_RANK];
   double mx = 0.0;
   for (int k = 0; k < R; ++k) mx = fmax(mx, fabs(A[k * R + k]));
   const double cut = 1e-15 * mx;
+  for (int k = tid; k < R; k += nt) ev[k] = A[k * R + k];
+  __syncthreads();
   for (int e = tid; e < RR; e += nt) {
-    const int i = e >> lgR, j = e & (R - 1);
-    double acc = 0.0;
-    for (int k = 0; k < R; ++k) {
-      const double lk = A[k * R + k];
-      if (fabs(lk) > cut) acc += Q[i * R + k] * Q[j * R + k] / lk;
-    }
-    Y[e] = acc;
+    const int i = e >> lgR, k = e & (R - 1);
+    const double lk = ev[k];
+    Y[e] = fabs(lk) > cut ? Q[i * R + k] / sqrt(fabs(lk)) : 0.0;            // F[i][k]
+    const double li = ev[i];
+    A[e] = fabs(li) > cut ? copysign(1.0 / sqrt(fabs(li)), li) * Q[k * R + i] : 0.0;  // G[i][k]
   }
   __syncthreads();
   return true;
 }
 
 // V = Hadamard product of the other modes' Grams, its Cholesky factor L
-// (V = L L^T), X = L^-1, V^-1 = X^T X and W = diag(Sn) V^-1, all in fp64
+// (V = L L^T), X = L^-1 and the solve factors W1 = diag(Sn) X^T, W2 = X
+// (V^-1 = X^T X, never formed), all in fp64
 // inside one CTA. Every elimination step is one pass over the R x R square
 // followed by one barrier: a thread recomputes the pivot quantities it needs
 // from values that are final before the step, and each step writes only
@@ -175,10 +179,16 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     }
     __syncthreads();
   }
+  // The solve leaves as two factors F G = V^-1 (or V^+), never as the
+  // explicit inverse: B_n = (M F) G keeps the error of each fp32 product near
+  // sqrt(cond V) times the rounding instead of cond V (on the 1e8-nonzero
+  // Zipf tensor, iteration 1's last V has cond 1.4e6, and M V^-1 formed in
+  // fp32 moved the fit by 8e-4; the two factors by 2e-7).
+  //   Cholesky V = L L^T: F = X^T, G = X with X = L^-1;
+  //   otherwise (the pseudo-inverse, as Alg. 1 states it): F and G from the
+  //   eigendecomposition of V (fp64 Jacobi).
+  // F goes to Y, G to V; only a V with a non-finite entry ends the run.
   if (!spd) {
-    // V is not positive definite: the pseudo-inverse, as Alg. 1 states it,
-    // from the eigendecomposition of V (fp64 Jacobi). Only a V with a
-    // non-finite entry ends the run.
     for (int e = tid; e < RR; e += nt) {
       double v = 1.0;
       for (int m = 0; m < a.N; ++m)
@@ -195,28 +205,29 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     }
     if (tid == 0) atomicOr(a.status, kStatusPinv);
   } else {
-  // X = L^-1 by forward substitution on Y = I: step k finalises row k of X
-  // (into V) and removes column k of L from the rows below.
-  for (int k = 0; k < R; ++k) {
-    const double inv = s_rs[k];  // 1 / L[k][k] = 1 / sqrt(d_k)
+    // X = L^-1 by forward substitution on Y = I: step k finalises row k of X
+    // (into V) and removes column k of L from the rows below.
+    for (int k = 0; k < R; ++k) {
+      const double inv = s_rs[k];  // 1 / L[k][k] = 1 / sqrt(d_k)
+      for (int e = tid; e < RR; e += nt) {
+        const int i = e >> lgR, c = e & (R - 1);
+        if (c > k || i < k) continue;
+        const double xk = Y[k * R + c] * inv;
+        if (i == k) V[e] = xk;
+        else Y[e] -= L[i * R + k] * xk;
+      }
+      __syncthreads();
+    }
+    // X is lower triangular: zero above the diagonal, F = X^T
     for (int e = tid; e < RR; e += nt) {
       const int i = e >> lgR, c = e & (R - 1);
-      if (c > k || i < k) continue;
-      const double xk = Y[k * R + c] * inv;
-      if (i == k) V[e] = xk;
-      else Y[e] -= L[i * R + k] * xk;
+      if (c > i) V[e] = 0.0;
     }
     __syncthreads();
-  }
-  // V^-1 = X^T X (X lower triangular): entry (p, q) sums rows k >= max(p, q)
-  for (int e = tid; e < RR; e += nt) {
-    const int p = e >> lgR, q = e & (R - 1);
-    if (q > p) continue;
-    double acc = 0.0;
-    for (int k = p; k < R; ++k) acc += V[k * R + p] * V[k * R + q];
-    Y[p * R + q] = acc;
-    Y[q * R + p] = acc;
-  }
+    for (int e = tid; e < RR; e += nt) {
+      const int i = e >> lgR, c = e & (R - 1);
+      Y[e] = V[c * R + i];
+    }
   }
   for (int r = tid; r < R; r += nt) {
     double p = 1.0;
@@ -225,20 +236,31 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     a.Sn[r] = p;
   }
   __syncthreads();
-  // W = diag(Sn) V^-1 in fp64 (in Y), stored in fp32. Sn multiplies the
-  // other modes' deferred scales and can leave the fp32 range although the
-  // solve is well defined: a column whose largest entry is outside
-  // [2^-60, 2^60] is divided by a power of two near it (undone in fp64 by
-  // finish_body). Other columns keep scale 1, so that B_n = M V^-1 keeps its
-  // natural magnitude (the column norms lambda).
+  // W1 = diag(Sn) F and W2 = G, stored in fp32 (W1 then W2). Sn multiplies
+  // the other modes' deferred scales and can leave the fp32 range although
+  // the solve is well defined: a column of W1 whose largest entry is outside
+  // [2^-60, 2^60] is divided by a power of two near it (the same power
+  // multiplies the matching row of W2), and so is a column of W2 (undone in
+  // fp64 by finish_body through wcol). Other columns keep scale 1, so that
+  // B_n = M W1 W2 keeps its natural magnitude (the column norms lambda).
   for (int e = tid; e < RR; e += nt) Y[e] *= a.Sn[e >> lgR];
   __syncthreads();
   __shared__ int bad;
+  __shared__ double ycol[ALTO_MAX_RANK];
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int c = tid; c < R; c += nt) {
     double mx = 0.0;
     for (int k = 0; k < R; ++k) mx = fmax(mx, fabs(Y[k * R + c]));
+    if (!isfinite(mx)) bad = 1;
+    ycol[c] = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ldexp(1.0, ilogb(mx)) : 1.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < RR; e += nt) V[e] *= ycol[e >> lgR];
+  __syncthreads();
+  for (int c = tid; c < R; c += nt) {
+    double mx = 0.0;
+    for (int k = 0; k < R; ++k) mx = fmax(mx, fabs(V[k * R + c]));
     if (!isfinite(mx)) bad = 1;
     a.wcol[c] = (mx > 0.0 && isfinite(mx) && (mx > 0x1p60 || mx < 0x1p-60)) ? ldexp(1.0, ilogb(mx)) : 1.0;
   }
@@ -250,17 +272,40 @@ __device__ __forceinline__ void prepare_body(const CpArgs &a, double *sd) {
     }
     return;
   }
-  for (int e = tid; e < RR; e += nt) a.W[e] = (float)(Y[e] / a.wcol[e & (R - 1)]);
+  for (int e = tid; e < RR; e += nt) {
+    a.W[e] = (float)(Y[e] / ycol[e & (R - 1)]);
+    a.W[RR + e] = (float)(V[e] / a.wcol[e & (R - 1)]);
+  }
 }
 
-// B = M W with B^T B and the column dot products of M and B, one pass.
+// B = (M W1) W2 with B^T B and the column dot products of M and B, one pass.
 // A tile of TR = 4096 / R rows: every thread computes a 4-row x 4-column block
-// of B from the transposed M tile and W (two 16-byte shared loads per 16
-// FMAs), adds its block's column products M(r,c) B(r,c), stores B, and then
+// of Y = M W1 from the transposed M tile (two 16-byte shared loads per 16
+// FMAs), puts it in shared memory, computes its block of B = Y W2 the same
+// way, adds its block's column products M(r,c) B(r,c), stores B, and then
 // accumulates a 4 x 4 block of B^T B over its share of the tile's rows.
 // fp32 partial sums cover at most 32 tiles per thread before they move to
 // fp64. The CTA walks tiles t0, t0 + tstep, ... < t1 (TR rows each); with
 // clear_m it also zeroes the M rows it has read.
+
+// o = the 4 x 4 block (rows 4 rb.., columns 4 cb..) of T W, T given
+// transposed in shared memory (column k of T at t + k * ld), W row-major R x R
+__device__ __forceinline__ void block_product(const float *t, int ld, const float *w, int R, int rb, int cb,
+                                              float (&o)[4][4]) {
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
+  for (int k = 0; k < R; ++k) {
+    const float4 tk = *reinterpret_cast<const float4 *>(t + k * ld + 4 * rb);
+    const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + 4 * cb);
+    const float ta[4] = {tk.x, tk.y, tk.z, tk.w}, wa[4] = {wk.x, wk.y, wk.z, wk.w};
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) o[x][y] = fmaf(ta[x], wa[y], o[x][y]);
+  }
+}
 
 // SYM: the Gram pass forms only the blocks of B^T B on and above the diagonal
 // (B4 (B4 + 1) / 2 of the B4^2 4 x 4 blocks) and mirrors them at the end;
@@ -278,9 +323,9 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
   const int TRP = TR + 4;        // padded row count of the transposed tile
   const int RP = R + 4;          // padded row length of the B tile
   double *red = reinterpret_cast<double *>(smraw);       // R*R + R
-  float *w = reinterpret_cast<float *>(red + R * R + R);  // R*R
-  float *mt = w + R * R;                                  // R * TRP (M tile, transposed)
-  float *bt = mt + R * TRP;                               // TR * RP (B tile)
+  float *w = reinterpret_cast<float *>(red + R * R + R);  // 2 R*R: W1, W2
+  float *mt = w + 2 * R * R;                              // R * TRP (M tile, transposed)
+  float *bt = mt + R * TRP;                               // TR * RP (B tile; first M W1, transposed)
   const int tid = threadIdx.x;
   const int B4 = R / 4;                      // column blocks
   const int cb = tid % B4, rb = tid / B4;    // phase 1: rows 4*rb .. 4*rb+3, cols 4*cb ..
@@ -298,7 +343,7 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
   }
   const bool gram = rg < RG;  // SYM leaves kUpdThreads mod BB threads out
   for (int i = tid; i < R * R + R; i += kUpdThreads) red[i] = 0.0;
-  for (int i = tid; i < R * R; i += kUpdThreads) w[i] = W[i];
+  for (int i = tid; i < 2 * R * R; i += kUpdThreads) w[i] = W[i];
   float g[4][4], dp[4];
   double dg[4][4], ddp[4];
 #pragma unroll
@@ -346,19 +391,15 @@ __device__ __forceinline__ void update_body(float *M, const float *__restrict__ 
     if (t + tstep < t1) load_tile(t + tstep);
     __syncthreads();
     float o[4][4];
+    // Y = M W1 (its block goes to shared memory, transposed like M), then
+    // B = Y W2
+    block_product(mt, TRP, w, R, rb, cb, o);
 #pragma unroll
-    for (int x = 0; x < 4; ++x)
-#pragma unroll
-      for (int y = 0; y < 4; ++y) o[x][y] = 0.f;
-    for (int k = 0; k < R; ++k) {
-      const float4 mk = *reinterpret_cast<const float4 *>(mt + k * TRP + 4 * rb);
-      const float4 wk = *reinterpret_cast<const float4 *>(w + k * R + 4 * cb);
-      const float ma[4] = {mk.x, mk.y, mk.z, mk.w}, wa[4] = {wk.x, wk.y, wk.z, wk.w};
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) o[x][y] = fmaf(ma[x], wa[y], o[x][y]);
-    }
+    for (int y = 0; y < 4; ++y)
+      *reinterpret_cast<float4 *>(bt + (4 * cb + y) * TRP + 4 * rb) = make_float4(o[0][y], o[1][y], o[2][y], o[3][y]);
+    __syncthreads();
+    block_product(bt, TRP, w + R * R, R, rb, cb, o);
+    __syncthreads();  // every read of Y is done before B overwrites it
     // column products with M, store B (global and shared)
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
