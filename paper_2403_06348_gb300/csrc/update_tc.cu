@@ -134,10 +134,11 @@ constexpr uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// x rounded to the nearest TF32 value (10 explicit mantissa bits), ties away
+// from zero, as an fp32 bit pattern with the 13 low bits clear: add half a
+// TF32 unit to the magnitude bits, then truncate (integer operations only)
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // byte offset of element (row, k) in a K-major operand (no swizzle)
@@ -156,49 +157,64 @@ struct TcLayout {
   // W1 (hi, lo), W2 (hi, lo), the A operand (M, then Y; hi, lo), the Gram operand (hi, lo)
   static constexpr uint32_t w1h = 0, w1l = kW, w2h = 2 * kW, w2l = 3 * kW;
   static constexpr uint32_t ah = 4 * kW, al = ah + kA, gh = al + kA, gl = gh + kG;
-  static constexpr uint32_t gsum = gl + kG;                    // R x R doubles
-  static constexpr uint32_t dsum = gsum + R * R * 8;          // R doubles
-  static constexpr uint32_t bar = dsum + R * 8;               // two mbarriers
+  static constexpr uint32_t bar = gl + kG;                    // two mbarriers
   static constexpr uint32_t tmem = bar + 16;                  // allocated address
   // at least 80 KB, so that at most two CTAs (2 x 256 tensor-memory columns)
   // share an SM and no allocation waits
   static constexpr uint32_t total = tmem + 16 > 80 * 1024 ? tmem + 16 : 80 * 1024;
 };
 
-// adds the diagonal R x R blocks D of the Gram accumulator (chunk q: lanes
-// and columns [q R, q R + R)) to gsum in fp64, symmetrised: the accumulator
-// holds hi hi^T + 2 hi lo^T, whose symmetric part (D + D^T) / 2 is
-// hi hi^T + hi lo^T + lo hi^T
+// Moves the diagonal R x R blocks D of the Gram accumulator (chunk q: lanes
+// and columns [q R, q R + R)) and the dot sums into the fp64 registers greg
+// (elements tid + 128 j of B^T B) and dreg (dot r = tid), through the free
+// Gram operand buffers (stage, dstage) in shared memory: no shared atomics.
+// The accumulator holds hi hi^T + 2 hi lo^T; its symmetric part (D + D^T) / 2
+// is hi hi^T + hi lo^T + lo hi^T.
 template <int R>
-__device__ __forceinline__ void flush_gram(uint32_t tbase, double *gsum, int warp, int lane) {
-  const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + kTcGramCol + 32u * warp;
-  const int i = 32 * warp + lane;  // tensor-memory lane = (q, r)
-  const int r = i % R, q = i / R;
-  const int first = q * R - 32 * warp;  // first needed column inside the 32 loaded
-  float v[32];
-  tmem_ld32(taddr, v);
+__device__ __forceinline__ void flush_sums(uint32_t tbase, float *stage, float *dstage, float (&dacc)[R],
+                                           double (&greg)[R * R / kTcThreads], double &dreg, int warp,
+                                           int lane, bool gram) {
+  const int tid = threadIdx.x;
+  if (gram) {
+    const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16) + kTcGramCol + 32u * warp;
+    const int i = 32 * warp + lane;  // tensor-memory lane = (q, r)
+    const int r = i % R, q = i / R;
+    const int first = q * R - 32 * warp;  // first needed column inside the 32 loaded
+    float v[32];
+    tmem_ld32(taddr, v);
+    // stage[q][r][c], rows padded to R + 1 (one column of the lanes: distinct banks)
 #pragma unroll
-  for (int c = 0; c < 32; ++c)
-    if (c >= first && c < first + R) {
-      const double h = 0.5 * (double)v[c];
-      atomicAdd(&gsum[r * R + (c - first)], h);
-      atomicAdd(&gsum[(c - first) * R + r], h);
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void flush_dots(float (&dacc)[R], double *dsum, int lane) {
+    for (int c = 0; c < 32; ++c)
+      if (c >= first && c < first + R) stage[(q * R + r) * (R + 1) + (c - first)] = v[c];
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     float v = dacc[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) atomicAdd(&dsum[r], (double)v);
+    if (lane == 0) dstage[warp * R + r] = v;
     dacc[r] = 0.f;
   }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < R * R / kTcThreads; ++j) {
+    if (!gram) break;
+    const int e = tid + kTcThreads * j, r = e / R, c = e % R;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < kTcRows / R; ++q)
+      acc += (double)stage[(q * R + r) * (R + 1) + c] + (double)stage[(q * R + c) * (R + 1) + r];
+    greg[j] += 0.5 * acc;
+  }
+  if (tid < R) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < kTcThreads / 32; ++w) acc += (double)dstage[w * R + tid];
+    dreg += acc;
+  }
+  __syncthreads();  // the buffers serve as Gram operands again
 }
 
-// row `row` of a K-major operand (hi and lo halves at bh, bl), split
 // chunk (row, 4 c .. 4 c + 3) of the A operand, split into its hi and lo halves
 template <int R>
 __device__ __forceinline__ void split_chunk(unsigned char *sm, int row, int c, float4 x) {
@@ -282,8 +298,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   using L = TcLayout<R>;
   if (*done_at <= it) return;
   extern __shared__ __align__(128) unsigned char sm[];
-  double *gsum = reinterpret_cast<double *>(sm + L::gsum);
-  double *dsum = reinterpret_cast<double *>(sm + L::dsum);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm + L::bar);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + L::tmem);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -307,8 +321,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     *reinterpret_cast<float *>(sm + o) = h;
     *reinterpret_cast<float *>(sm + o + L::kW) = tf32_rna(x - h);
   }
-  for (int e = tid; e < R * R; e += kTcThreads) gsum[e] = 0.0;
-  for (int e = tid; e < R; e += kTcThreads) dsum[e] = 0.0;
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -321,6 +333,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   float dacc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) dacc[r] = 0.f;
+  double greg[R * R / kTcThreads], dreg = 0.0;
+#pragma unroll
+  for (int j = 0; j < R * R / kTcThreads; ++j) greg[j] = 0.0;
+  float *stage = reinterpret_cast<float *>(sm + L::gh), *dstage = reinterpret_cast<float *>(sm + L::gl);
   // the tile's rows arrive coalesced: warp w loads rows 32 w .. 32 w + 31,
   // lane j the 16-byte chunks e = 32 v + j (row e / (R/4), chunk e % (R/4))
   constexpr int kChunks = R / 4;
@@ -380,12 +396,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
     if (since_flush == kTcFlush) {
       tc_fence_after();
-      flush_gram<R>(tbase, gsum, warp, lane);
-      flush_dots<R>(dacc, dsum, lane);
+      flush_sums<R>(tbase, stage, dstage, dacc, greg, dreg, warp, lane, true);
       since_flush = 0;
     }
     {
-      // G[(q, r)][k] = B[q R + k][r]: hi, and 2 lo (see flush_gram)
+      // G[(q, r)][k] = B[q R + k][r]: hi, and 2 lo (see flush_sums)
       const int q = tid / R, k = tid % R;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -442,21 +457,18 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     if (tid == 0) atomicOr(status, kStatusTimeout);
     since_flush = 0;  // the accumulator is not complete: not read
   }
-  if (since_flush > 0) {
-    tc_fence_after();
-    flush_gram<R>(tbase, gsum, warp, lane);
-  }
-  flush_dots<R>(dacc, dsum, lane);
+  tc_fence_after();
+  flush_sums<R>(tbase, stage, dstage, dacc, greg, dreg, warp, lane, since_flush > 0);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tbase, kTcCols);
   }
-  for (int e = tid; e < R * R; e += kTcThreads)
-    if (gsum[e] != 0.0) atomicAdd(&BtB[e], gsum[e]);
-  for (int e = tid; e < R; e += kTcThreads)
-    if (dsum[e] != 0.0) atomicAdd(&dot[e], dsum[e]);
+#pragma unroll
+  for (int j = 0; j < R * R / kTcThreads; ++j)
+    if (greg[j] != 0.0) atomicAdd(&BtB[tid + kTcThreads * j], greg[j]);
+  if (tid < R && dreg != 0.0) atomicAdd(&dot[tid], dreg);
 }
 
 template <int R>
